@@ -1,0 +1,452 @@
+/*
+ * CPU oracle for the Generic Join prefix-extension method. TEST
+ * INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark call it; the library path never does.
+ *
+ * Plain, slow and single threaded on purpose. It shares no code with the
+ * CUDA path. Every function says which part of the paper it follows:
+ *   - relations and queries: Section 1 and Section 2.1 (a subgraph query is
+ *     a multiway self-join of the edge relation under join semantics);
+ *   - extension indices Ext^i_j with size, enumeration and membership:
+ *     Section 2.2;
+ *   - Generic Join from P0 = {()} to Pm, proposing from the smallest
+ *     extension set and intersecting with the others: Fig. 1, Section 2.2;
+ *   - delta queries dQ_1..dQ_n with new versions before i and old versions
+ *     after i, seeded from the signed changes Delta R_i: Section 3.3.1
+ *     (Delta-GJ) and Section 4.3;
+ *   - update semantics R' = R + Delta R (a deletion removes the tuple):
+ *     Section 3.3.1.
+ *
+ * The match checksum is not from the paper; it is the order-independent sum
+ * (mod 2^64) over matches of H(x_1..x_k), H built from the SplitMix64 output
+ * function (Steele, Lea, Flood, OOPSLA 2014), with the tuple in query
+ * attribute order.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OG_MAX_K 8
+#define OG_MAX_ATOMS 16
+
+enum { OG_OK = 0, OG_E_INVALID = -1, OG_E_RANGE = -2, OG_E_NOMEM = -3, OG_E_TRUNCATED = -5 };
+
+/* ---------------------------------------------------------------- graph */
+
+typedef struct {
+    uint32_t n;          /* vertices are 0..n-1 */
+    uint64_t m;          /* distinct edges, no self-loops */
+    uint64_t* fo;        /* forward offsets [n+1] */
+    uint32_t* fn;        /* out-neighbours, sorted per vertex */
+    uint64_t* ro;        /* reverse offsets [n+1] */
+    uint32_t* rn;        /* in-neighbours, sorted per vertex */
+    uint32_t* srcs;      /* vertices with out-degree > 0, ascending */
+    uint64_t nsrcs;
+    uint32_t* dsts;      /* vertices with in-degree > 0, ascending */
+    uint64_t ndsts;
+} og_graph;
+
+static int cmp_u64(const void* a, const void* b) {
+    uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+    return (x > y) - (x < y);
+}
+
+/* Sorted distinct keys (hi << 32 | lo) from the pairs, self-loops dropped. */
+static uint64_t sorted_keys(const uint32_t* hi, const uint32_t* lo, uint64_t m, uint64_t* keys) {
+    uint64_t c = 0;
+    for (uint64_t i = 0; i < m; i++)
+        if (hi[i] != lo[i]) keys[c++] = ((uint64_t)hi[i] << 32) | lo[i];
+    qsort(keys, c, sizeof(uint64_t), cmp_u64);
+    uint64_t u = 0;
+    for (uint64_t i = 0; i < c; i++)
+        if (u == 0 || keys[i] != keys[u - 1]) keys[u++] = keys[i];
+    return u;
+}
+
+/* Adjacency lists keyed by the high half of each key (an extension index, Section 2.2). */
+static void lists_from_keys(uint32_t n, const uint64_t* keys, uint64_t m, uint64_t* off, uint32_t* nbr) {
+    memset(off, 0, sizeof(uint64_t) * ((size_t)n + 1));
+    for (uint64_t i = 0; i < m; i++) off[(keys[i] >> 32) + 1]++;
+    for (uint32_t v = 0; v < n; v++) off[v + 1] += off[v];
+    for (uint64_t i = 0; i < m; i++) nbr[i] = (uint32_t)keys[i];
+}
+
+void og_graph_free(og_graph* g) {
+    if (!g) return;
+    free(g->fo); free(g->fn); free(g->ro); free(g->rn); free(g->srcs); free(g->dsts);
+    free(g);
+}
+
+/*
+ * The edge relation: distinct (src, dst) pairs, self-loops dropped, with a
+ * forward index (out-neighbours of each vertex) and a reverse index
+ * (in-neighbours), the two indices of Section 4.1. Returns NULL on a vertex
+ * id >= n (*err = OG_E_RANGE) or when memory runs out.
+ */
+og_graph* og_graph_new(uint32_t n, const uint32_t* src, const uint32_t* dst, uint64_t m, int* err) {
+    *err = OG_OK;
+    for (uint64_t i = 0; i < m; i++)
+        if (src[i] >= n || dst[i] >= n) { *err = OG_E_RANGE; return NULL; }
+    og_graph* g = (og_graph*)calloc(1, sizeof(og_graph));
+    uint64_t* keys = (uint64_t*)malloc(sizeof(uint64_t) * (m ? m : 1));
+    if (!g || !keys) { free(g); free(keys); *err = OG_E_NOMEM; return NULL; }
+    g->n = n;
+    g->fo = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    g->ro = (uint64_t*)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    uint64_t mf = sorted_keys(src, dst, m, keys);
+    g->m = mf;
+    g->fn = (uint32_t*)malloc(sizeof(uint32_t) * (mf ? mf : 1));
+    g->rn = (uint32_t*)malloc(sizeof(uint32_t) * (mf ? mf : 1));
+    if (!g->fo || !g->ro || !g->fn || !g->rn) { free(keys); og_graph_free(g); *err = OG_E_NOMEM; return NULL; }
+    lists_from_keys(n, keys, mf, g->fo, g->fn);
+    uint64_t mr = sorted_keys(dst, src, m, keys);
+    (void)mr; /* mr == mf: the same pair set, transposed */
+    lists_from_keys(n, keys, mf, g->ro, g->rn);
+    free(keys);
+    g->srcs = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    g->dsts = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)n + 1));
+    if (!g->srcs || !g->dsts) { og_graph_free(g); *err = OG_E_NOMEM; return NULL; }
+    for (uint32_t v = 0; v < n; v++) {
+        if (g->fo[v + 1] > g->fo[v]) g->srcs[g->nsrcs++] = v;
+        if (g->ro[v + 1] > g->ro[v]) g->dsts[g->ndsts++] = v;
+    }
+    return g;
+}
+
+uint64_t og_graph_num_edges(const og_graph* g) { return g->m; }
+
+/* The distinct edges in (src, dst) order. */
+void og_graph_edges(const og_graph* g, uint32_t* src, uint32_t* dst) {
+    for (uint32_t v = 0; v < g->n; v++)
+        for (uint64_t i = g->fo[v]; i < g->fo[v + 1]; i++) { src[i] = v; dst[i] = g->fn[i]; }
+}
+
+/* Membership of e in a sorted list (binary search): property (iii) of Section 2.2. */
+static int in_list(const uint32_t* a, uint64_t len, uint32_t e) {
+    uint64_t lo = 0, hi = len;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < e) lo = mid + 1; else hi = mid;
+    }
+    return lo < len && a[lo] == e;
+}
+
+static int has_edge(const og_graph* g, uint32_t u, uint32_t v) {
+    return in_list(g->fn + g->fo[u], g->fo[u + 1] - g->fo[u], v);
+}
+
+/* ---------------------------------------------------------------- query */
+
+typedef struct {
+    uint32_t k, natoms;
+    uint32_t as[OG_MAX_ATOMS], ad[OG_MAX_ATOMS];  /* atom t is E(a_as[t], a_ad[t]) */
+    uint32_t order[OG_MAX_K];                     /* global attribute order */
+} og_query;
+
+/* A query Q(a_0..a_{k-1}) := E(a_s, a_d), ... (Section 2.1). 0 or OG_E_INVALID. */
+static int make_query(uint32_t k, const uint32_t* atoms, uint32_t natoms, const uint32_t* order, og_query* q) {
+    if (k < 1 || k > OG_MAX_K || natoms < 1 || natoms > OG_MAX_ATOMS || !atoms) return OG_E_INVALID;
+    q->k = k; q->natoms = natoms;
+    uint32_t used = 0;
+    for (uint32_t t = 0; t < natoms; t++) {
+        q->as[t] = atoms[2 * t]; q->ad[t] = atoms[2 * t + 1];
+        if (q->as[t] >= k || q->ad[t] >= k || q->as[t] == q->ad[t]) return OG_E_INVALID;
+        used |= (1u << q->as[t]) | (1u << q->ad[t]);
+    }
+    if (used != (1u << k) - 1) return OG_E_INVALID;  /* every attribute is in some atom */
+    uint32_t seen = 0;
+    for (uint32_t j = 0; j < k; j++) {
+        uint32_t a = order ? order[j] : j;
+        if (a >= k || (seen & (1u << a))) return OG_E_INVALID;
+        seen |= 1u << a;
+        q->order[j] = a;
+    }
+    return OG_OK;
+}
+
+/* ------------------------------------------------------------ checksum */
+
+static uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* H of a match, tuple in query attribute order a_0..a_{k-1}. */
+static uint64_t tuple_hash(uint32_t k, const uint32_t* x_by_attr) {
+    uint64_t h = mix64(k);
+    for (uint32_t a = 0; a < k; a++) h = mix64(h ^ (uint64_t)x_by_attr[a]);
+    return h;
+}
+
+uint64_t og_mix64(uint64_t z) { return mix64(z); }
+uint64_t og_tuple_hash(uint32_t k, const uint32_t* x) { return tuple_hash(k, x); }
+
+/* ---------------------------------------------------------- Generic Join */
+
+/*
+ * Instrumentation of the prefix-extension work, in the units of the cost
+ * model of Section 2.2 / Theorem 2.1 (one size lookup per binding relation
+ * per prefix, one proposal per element of the smallest extension set, one
+ * membership test per proposal per other binding relation). Index j is the
+ * prefix length being extended.
+ */
+typedef struct {
+    int64_t prefixes[OG_MAX_K + 1];   /* |P_j| reached */
+    int64_t extended[OG_MAX_K + 1];   /* prefixes of length j that were extended */
+    int64_t nbind_sum[OG_MAX_K + 1];  /* sum over those of the number of binding relations */
+    int64_t proposals[OG_MAX_K + 1];  /* sum of min-c */
+    int64_t probes[OG_MAX_K + 1];     /* membership tests */
+} og_stats;
+
+/* The relations (atoms) that one dQ_i evaluation sees (Section 3.3.1). */
+typedef struct {
+    const og_graph* view[OG_MAX_ATOMS];  /* graph each atom reads; NULL for the Delta atom */
+} og_views;
+
+typedef struct {
+    const og_query* q;
+    const og_views* v;
+    uint32_t order[OG_MAX_K];   /* execution order (attribute ids) */
+    uint32_t pos[OG_MAX_K];     /* pos[a] = position of attribute a in the execution order */
+    uint32_t x[OG_MAX_K];       /* x[a] = value bound to attribute a */
+    uint32_t first_lo, first_hi;/* value range allowed for the first attribute */
+    int sign;                   /* +1, or the sign of the Delta tuple that seeded this run */
+    int64_t count;
+    uint64_t chk;
+    og_stats* st;
+    uint32_t* out; uint64_t cap, written;  /* optional listing, tuples in query order */
+} og_run;
+
+/* One extension set Ext^t_j(p) for attribute A of atom t: a sorted list. */
+typedef struct { const uint32_t* a; uint64_t len; } og_set;
+
+static og_set ext_set(const og_run* r, uint32_t t, uint32_t A, uint32_t j) {
+    const og_query* q = r->q;
+    const og_graph* g = r->v->view[t];
+    og_set s;
+    uint32_t B = (q->as[t] == A) ? q->ad[t] : q->as[t];
+    if (r->pos[B] < j) {
+        uint32_t vb = r->x[B];
+        if (q->ad[t] == A) { s.a = g->fn + g->fo[vb]; s.len = g->fo[vb + 1] - g->fo[vb]; }   /* E(B, A): out(B) */
+        else { s.a = g->rn + g->ro[vb]; s.len = g->ro[vb + 1] - g->ro[vb]; }                  /* E(A, B): in(B) */
+    } else {
+        /* B comes later: the relation restricted to the first j+1 attributes is its projection on A */
+        if (q->as[t] == A) { s.a = g->srcs; s.len = g->nsrcs; }
+        else { s.a = g->dsts; s.len = g->ndsts; }
+    }
+    return s;
+}
+
+static void emit(og_run* r) {
+    const og_query* q = r->q;
+    r->count += r->sign;
+    uint64_t h = tuple_hash(q->k, r->x);
+    r->chk += (r->sign > 0) ? h : (uint64_t)(0 - h);
+    if (r->out) {
+        if (r->written < r->cap)
+            for (uint32_t a = 0; a < q->k; a++) r->out[r->written * q->k + a] = r->x[a];
+        r->written++;
+    }
+}
+
+/*
+ * Extend every prefix of length j (attributes order[0..j-1] bound) by
+ * attribute order[j], as in Fig. 1: the relations that contain the new
+ * attribute each give an extension set; the smallest one proposes (ties go
+ * to the lowest atom index), and each proposal is kept only if it is a
+ * member of every other set. Relations not yet joined at this level (none
+ * of their attributes bound) do not constrain it.
+ */
+static void gj_extend(og_run* r, uint32_t j) {
+    const og_query* q = r->q;
+    if (r->st) r->st->prefixes[j]++;
+    if (j == q->k) { emit(r); return; }
+    uint32_t A = r->order[j];
+    og_set sets[OG_MAX_ATOMS];
+    uint32_t nsets = 0, imin = 0;
+    for (uint32_t t = 0; t < q->natoms; t++) {
+        if (r->v->view[t] == NULL) continue;            /* the Delta atom was consumed by the seed */
+        if (q->as[t] != A && q->ad[t] != A) continue;   /* does not contain a_{j+1} */
+        sets[nsets] = ext_set(r, t, A, j);
+        if (sets[nsets].len < sets[imin].len) imin = nsets;
+        nsets++;
+    }
+    if (nsets == 0) return;  /* cannot happen for a validated query */
+    if (r->st) {
+        r->st->extended[j]++;
+        r->st->nbind_sum[j] += nsets;
+        r->st->proposals[j] += (int64_t)sets[imin].len;
+    }
+    for (uint64_t c = 0; c < sets[imin].len; c++) {
+        uint32_t e = sets[imin].a[c];
+        if (j == 0 && (e < r->first_lo || e >= r->first_hi)) continue;
+        int ok = 1;
+        for (uint32_t s = 0; s < nsets && ok; s++) {
+            if (s == imin) continue;
+            if (r->st) r->st->probes[j]++;
+            ok = in_list(sets[s].a, sets[s].len, e);
+        }
+        if (!ok) continue;
+        r->x[A] = e;
+        gj_extend(r, j + 1);
+    }
+}
+
+static void run_init(og_run* r, const og_query* q, const og_views* v, const uint32_t* order) {
+    memset(r, 0, sizeof(*r));
+    r->q = q; r->v = v; r->sign = 1;
+    for (uint32_t j = 0; j < q->k; j++) { r->order[j] = order[j]; r->pos[order[j]] = j; }
+    r->first_lo = 0; r->first_hi = UINT32_MAX;
+}
+
+/*
+ * Static evaluation: count and checksum of Q over g with GJ from P0 = {()}.
+ * Only matches whose first attribute (in execution order) lies in
+ * [first_lo, first_hi) are counted; the count is additive over such ranges.
+ * stats and out may be NULL. If out is given, up to cap tuples (query
+ * attribute order) are written and *written receives the total.
+ */
+int og_count(const og_graph* g, uint32_t k, const uint32_t* atoms, uint32_t natoms, const uint32_t* order,
+             uint32_t first_lo, uint32_t first_hi, int64_t* count, uint64_t* chk, og_stats* stats,
+             uint32_t* out, uint64_t cap, uint64_t* written) {
+    og_query q;
+    int rc = make_query(k, atoms, natoms, order, &q);
+    if (rc) return rc;
+    og_views v;
+    for (uint32_t t = 0; t < q.natoms; t++) v.view[t] = g;
+    og_run r;
+    run_init(&r, &q, &v, q.order);
+    r.first_lo = first_lo; r.first_hi = first_hi;
+    r.st = stats;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    r.out = out; r.cap = cap;
+    gj_extend(&r, 0);
+    *count = r.count;
+    *chk = r.chk;
+    if (written) *written = r.written;
+    return (out && r.written > cap) ? OG_E_TRUNCATED : OG_OK;
+}
+
+/* ------------------------------------------------------------- updates */
+
+typedef struct { uint64_t key; uint64_t idx; int8_t sign; } og_upd;
+
+static int cmp_upd(const void* a, const void* b) {
+    const og_upd* x = (const og_upd*)a; const og_upd* y = (const og_upd*)b;
+    if (x->key != y->key) return (x->key > y->key) - (x->key < y->key);
+    return (x->idx > y->idx) - (x->idx < y->idx);
+}
+
+/*
+ * Normalises a batch of signed edge updates against g under the set
+ * semantics R' = R + Delta R of Section 3.3.1: updates apply in batch
+ * order, so the last update of an edge decides whether it is present
+ * afterwards; self-loops are dropped; an edge's change is +1 if it was
+ * absent and ends present, -1 if it was present and ends absent, and it is
+ * dropped otherwise. Writes the changes sorted by (src, dst) and returns
+ * their number, or OG_E_RANGE / OG_E_INVALID (sign not +-1) / OG_E_NOMEM.
+ */
+int64_t og_normalize(const og_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign, uint64_t b,
+                     uint32_t* osrc, uint32_t* odst, int8_t* osign) {
+    og_upd* u = (og_upd*)malloc(sizeof(og_upd) * (b ? b : 1));
+    if (!u) return OG_E_NOMEM;
+    uint64_t c = 0;
+    for (uint64_t i = 0; i < b; i++) {
+        if (src[i] >= g->n || dst[i] >= g->n) { free(u); return OG_E_RANGE; }
+        if (sign[i] != 1 && sign[i] != -1) { free(u); return OG_E_INVALID; }
+        if (src[i] == dst[i]) continue;
+        u[c].key = ((uint64_t)src[i] << 32) | dst[i]; u[c].idx = i; u[c].sign = sign[i]; c++;
+    }
+    qsort(u, c, sizeof(og_upd), cmp_upd);
+    int64_t nout = 0;
+    for (uint64_t i = 0; i < c; i++) {
+        if (i + 1 < c && u[i + 1].key == u[i].key) continue;  /* a later update of this edge decides */
+        uint32_t s = (uint32_t)(u[i].key >> 32), d = (uint32_t)u[i].key;
+        int present = has_edge(g, s, d);
+        if ((u[i].sign > 0) == present) continue;              /* no change */
+        osrc[nout] = s; odst[nout] = d; osign[nout] = u[i].sign; nout++;
+    }
+    free(u);
+    return nout;
+}
+
+/* The graph after applying normalised changes (R' = R + Delta R). */
+og_graph* og_graph_apply(const og_graph* g, const uint32_t* dsrc, const uint32_t* ddst, const int8_t* dsign,
+                         uint64_t nd, int* err) {
+    uint64_t cap = g->m + nd;
+    uint32_t* s = (uint32_t*)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+    uint32_t* d = (uint32_t*)malloc(sizeof(uint32_t) * (cap ? cap : 1));
+    if (!s || !d) { free(s); free(d); *err = OG_E_NOMEM; return NULL; }
+    uint8_t* gone = (uint8_t*)calloc(g->m ? g->m : 1, 1);
+    if (!gone) { free(s); free(d); *err = OG_E_NOMEM; return NULL; }
+    og_graph_edges(g, s, d);
+    /* find each deleted edge in the (sorted) edge list and flag it */
+    for (uint64_t i = 0; i < nd; i++) {
+        if (dsign[i] > 0) continue;
+        uint32_t u = dsrc[i];
+        uint64_t lo = g->fo[u], hi = g->fo[u + 1];
+        while (lo < hi) { uint64_t mid = lo + (hi - lo) / 2; if (d[mid] < ddst[i]) lo = mid + 1; else hi = mid; }
+        if (lo < g->fo[u + 1] && d[lo] == ddst[i]) gone[lo] = 1;
+    }
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < g->m; i++)
+        if (!gone[i]) { s[m] = s[i]; d[m] = d[i]; m++; }
+    free(gone);
+    for (uint64_t i = 0; i < nd; i++)
+        if (dsign[i] > 0) { s[m] = dsrc[i]; d[m] = ddst[i]; m++; }
+    og_graph* out = og_graph_new(g->n, s, d, m, err);
+    free(s); free(d);
+    return out;
+}
+
+/*
+ * Delta-GJ (Section 3.3.1): the change of Q's matches caused by the
+ * normalised changes Delta (dsrc, ddst, dsign) that turn g_old into g_new,
+ * as the sum of the delta queries
+ *     dQ_i := R'_1, ..., R'_{i-1}, Delta R_i, R_{i+1}, ..., R_n
+ * with atoms numbered in query definition order. Each dQ_i runs GJ with an
+ * attribute order that starts with the attributes of atom i (source, then
+ * destination) followed by the remaining attributes in the query's order
+ * (or in ascending attribute id when order is NULL), seeded from each
+ * signed change; every match counts with its seed's sign.
+ */
+int og_delta(const og_graph* g_old, const og_graph* g_new, const uint32_t* dsrc, const uint32_t* ddst,
+             const int8_t* dsign, uint64_t nd, uint32_t k, const uint32_t* atoms, uint32_t natoms,
+             const uint32_t* order, int64_t* dcount, uint64_t* dchk) {
+    og_query q;
+    int rc = make_query(k, atoms, natoms, order, &q);
+    if (rc) return rc;
+    int64_t total = 0;
+    uint64_t tchk = 0;
+    for (uint32_t i = 0; i < q.natoms; i++) {
+        og_views v;
+        for (uint32_t t = 0; t < q.natoms; t++) v.view[t] = (t < i) ? g_new : (t > i ? g_old : NULL);
+        uint32_t ord[OG_MAX_K], n = 0;
+        ord[n++] = q.as[i];
+        ord[n++] = q.ad[i];
+        for (uint32_t j = 0; j < q.k; j++)
+            if (q.order[j] != q.as[i] && q.order[j] != q.ad[i]) ord[n++] = q.order[j];
+        og_run r;
+        run_init(&r, &q, &v, ord);
+        for (uint64_t c = 0; c < nd; c++) {
+            r.x[q.as[i]] = dsrc[c];
+            r.x[q.ad[i]] = ddst[c];
+            r.sign = dsign[c];
+            /* the remaining atoms over the same two attributes filter the seed in their own versions */
+            int ok = 1;
+            for (uint32_t t = 0; t < q.natoms && ok; t++) {
+                if (t == i) continue;
+                uint32_t s = q.as[t], d = q.ad[t];
+                if ((s == q.as[i] || s == q.ad[i]) && (d == q.as[i] || d == q.ad[i]))
+                    ok = has_edge(v.view[t], r.x[s], r.x[d]);
+            }
+            if (ok) gj_extend(&r, 2);
+        }
+        total += r.count;
+        tchk += r.chk;
+    }
+    *dcount = total;
+    *dchk = tchk;
+    return OG_OK;
+}
