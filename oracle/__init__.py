@@ -83,7 +83,8 @@ def _load():
             lib.og_tuple_hash.argtypes = [ctypes.c_uint32, u32p]
             lib.og_count.restype = ctypes.c_int
             lib.og_count.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint32, u32p, ctypes.c_uint32,
-                                     ctypes.c_uint32, i64p, u64p, ctypes.POINTER(Stats), u32p, ctypes.c_uint64, u64p]
+                                     ctypes.c_uint32, ctypes.c_int, i64p, u64p, ctypes.POINTER(Stats), u32p,
+                                     ctypes.c_uint64, u64p]
             lib.og_normalize.restype = ctypes.c_int64
             lib.og_normalize.argtypes = [vp, u32p, u32p, i8p, ctypes.c_uint64, u32p, u32p, i8p]
             lib.og_graph_apply.restype = vp
@@ -176,14 +177,18 @@ class Graph:
                                d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
         return s, d
 
-    def count(self, q: Query, first_range=None, stats: bool = False):
-        """(count, checksum[, Stats]) of q; first_range = (lo, hi) limits the first attribute."""
+    def count(self, q: Query, first_range=None, stats: bool = False, mode: int = 0):
+        """(count, checksum[, Stats]) of q; first_range = (lo, hi) limits the first attribute.
+
+        mode 0: Generic Join from P0 as in Fig. 1 (the definition); mode 1:
+        the paper's implementation (edge seeds, bound atoms only, Section 4.1
+        and Section 4.2), whose work units the CUDA path reports."""
         lo, hi = first_range if first_range is not None else (0, 0xFFFFFFFF)
         c = ctypes.c_int64(0)
         h = ctypes.c_uint64(0)
         st = Stats() if stats else None
         pa, na, po = q._args()
-        _check(_load().og_count(self._h, q.k, pa, na, po, lo, hi, ctypes.byref(c), ctypes.byref(h),
+        _check(_load().og_count(self._h, q.k, pa, na, po, lo, hi, mode, ctypes.byref(c), ctypes.byref(h),
                                 ctypes.byref(st) if st is not None else None, None, 0, None))
         if stats:
             return c.value, h.value, st
@@ -198,7 +203,7 @@ class Graph:
         h = ctypes.c_uint64(0)
         w = ctypes.c_uint64(0)
         pa, na, po = q._args()
-        _check(_load().og_count(self._h, q.k, pa, na, po, 0, 0xFFFFFFFF, ctypes.byref(c), ctypes.byref(h), None,
+        _check(_load().og_count(self._h, q.k, pa, na, po, 0, 0xFFFFFFFF, 0, ctypes.byref(c), ctypes.byref(h), None,
                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap, ctypes.byref(w)))
         return out[:w.value], h.value
 

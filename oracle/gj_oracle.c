@@ -212,6 +212,7 @@ typedef struct {
     uint32_t x[OG_MAX_K];       /* x[a] = value bound to attribute a */
     uint32_t first_lo, first_hi;/* value range allowed for the first attribute */
     int sign;                   /* +1, or the sign of the Delta tuple that seeded this run */
+    int bound_only;             /* 1: only atoms whose other attribute is bound bind a level (Section 4.1) */
     int64_t count;
     uint64_t chk;
     og_stats* st;
@@ -268,6 +269,10 @@ static void gj_extend(og_run* r, uint32_t j) {
     for (uint32_t t = 0; t < q->natoms; t++) {
         if (r->v->view[t] == NULL) continue;            /* the Delta atom was consumed by the seed */
         if (q->as[t] != A && q->ad[t] != A) continue;   /* does not contain a_{j+1} */
+        if (r->bound_only) {
+            uint32_t B = (q->as[t] == A) ? q->ad[t] : q->as[t];
+            if (r->pos[B] >= j) continue;                /* its other attribute is not bound yet */
+        }
         sets[nsets] = ext_set(r, t, A, j);
         if (sets[nsets].len < sets[imin].len) imin = nsets;
         nsets++;
@@ -301,14 +306,29 @@ static void run_init(og_run* r, const og_query* q, const og_views* v, const uint
 }
 
 /*
- * Static evaluation: count and checksum of Q over g with GJ from P0 = {()}.
+ * Static evaluation: count and checksum of Q over g.
+ *
+ * mode 0 follows Fig. 1 and Section 2.2 literally: GJ from P0 = {()}, every
+ * relation containing the next attribute gives an extension set (its
+ * projection when its other attribute is not bound yet), so P_j is exactly
+ * the result of Q with every relation restricted to the first j attributes.
+ *
+ * mode 1 follows the paper's implementation (Section 4.1, Section 4.2):
+ * the length-2 prefixes are the edges of the first atom over the first two
+ * attributes of the order (kept if every other atom over those two
+ * attributes holds), and a level is bound only by the atoms whose other
+ * attribute is already bound. Both modes give the same matches; their
+ * intermediate prefix sets differ. Mode 1 needs an order whose first two
+ * attributes share an atom and whose later attributes each share an atom
+ * with an earlier one.
+ *
  * Only matches whose first attribute (in execution order) lies in
  * [first_lo, first_hi) are counted; the count is additive over such ranges.
  * stats and out may be NULL. If out is given, up to cap tuples (query
  * attribute order) are written and *written receives the total.
  */
 int og_count(const og_graph* g, uint32_t k, const uint32_t* atoms, uint32_t natoms, const uint32_t* order,
-             uint32_t first_lo, uint32_t first_hi, int64_t* count, uint64_t* chk, og_stats* stats,
+             uint32_t first_lo, uint32_t first_hi, int mode, int64_t* count, uint64_t* chk, og_stats* stats,
              uint32_t* out, uint64_t cap, uint64_t* written) {
     og_query q;
     int rc = make_query(k, atoms, natoms, order, &q);
@@ -321,7 +341,40 @@ int og_count(const og_graph* g, uint32_t k, const uint32_t* atoms, uint32_t nato
     r.st = stats;
     if (stats) memset(stats, 0, sizeof(*stats));
     r.out = out; r.cap = cap;
-    gj_extend(&r, 0);
+    if (mode == 0) {
+        gj_extend(&r, 0);
+    } else {
+        /* seed atom: the first atom over the first two attributes of the order */
+        uint32_t a0 = q.order[0], a1 = q.order[1];
+        int seed = -1;
+        for (uint32_t t = 0; t < q.natoms && seed < 0; t++)
+            if ((q.as[t] == a0 && q.ad[t] == a1) || (q.as[t] == a1 && q.ad[t] == a0)) seed = (int)t;
+        if (seed < 0) return OG_E_INVALID;
+        for (uint32_t j = 2; j < q.k; j++) {
+            int ok = 0;
+            for (uint32_t t = 0; t < q.natoms; t++) {
+                uint32_t ps = r.pos[q.as[t]], pd = r.pos[q.ad[t]];
+                if ((ps == j && pd < j) || (pd == j && ps < j)) ok = 1;
+            }
+            if (!ok) return OG_E_INVALID;
+        }
+        r.bound_only = 1;
+        for (uint32_t u = 0; u < g->n; u++) {
+            for (uint64_t e = g->fo[u]; e < g->fo[u + 1]; e++) {
+                uint32_t w = g->fn[e];
+                r.x[q.as[seed]] = u;
+                r.x[q.ad[seed]] = w;
+                if (r.x[a0] < first_lo || r.x[a0] >= first_hi) continue;
+                int ok = 1;
+                for (uint32_t t = 0; t < q.natoms && ok; t++) {
+                    if ((int)t == seed) continue;
+                    uint32_t ps = r.pos[q.as[t]], pd = r.pos[q.ad[t]];
+                    if (ps <= 1 && pd <= 1) ok = has_edge(g, r.x[q.as[t]], r.x[q.ad[t]]);
+                }
+                if (ok) gj_extend(&r, 2);
+            }
+        }
+    }
     *count = r.count;
     *chk = r.chk;
     if (written) *written = r.written;

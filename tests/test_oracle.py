@@ -88,6 +88,7 @@ def test_brute_force_named_queries(name, seed):
     g = og(n, edges)
     q = oracle.Query(k, atoms)
     assert g.count(q) == (want_c, want_h)
+    assert g.count(q, mode=1) == (want_c, want_h)
     got, h = g.list(q)
     assert {tuple(int(x) for x in t) for t in got} == want_set
     assert h == want_h
@@ -111,7 +112,20 @@ def test_brute_force_random_queries(seed):
     n = int(rng.integers(3, 7))
     edges = random_edges(rng, n, float(rng.uniform(0.2, 0.8)))
     want_c, want_h, _ = brute_force(n, edges, k, atoms)
-    assert og(n, edges).count(oracle.Query(k, atoms, order)) == (want_c, want_h)
+    g = og(n, edges)
+    assert g.count(oracle.Query(k, atoms, order)) == (want_c, want_h)
+    # the implementation's evaluation (edge seeds, bound atoms only) on every connected order
+    for o in itertools.permutations(range(k)):
+        if connected_order(atoms, o):
+            assert g.count(oracle.Query(k, atoms, o), mode=1) == (want_c, want_h), o
+
+
+def connected_order(atoms, order):
+    pos = {a: i for i, a in enumerate(order)}
+    if not any({pos[s], pos[d]} == {0, 1} for s, d in atoms):
+        return False
+    return all(any((pos[s] == j and pos[d] < j) or (pos[d] == j and pos[s] < j) for s, d in atoms)
+               for j in range(2, len(order)))
 
 
 @pytest.mark.parametrize("n", [5, 6, 8, 9])
@@ -219,17 +233,30 @@ def test_order_invariance(name):
         assert g.count(oracle.Query(k, atoms, order)) == ref, order
 
 
-def test_first_attribute_ranges_add_up():
+@pytest.mark.parametrize("mode", [0, 1])
+def test_first_attribute_ranges_add_up(mode):
     s, d = er_edges(300, 4000, seed=3)
     g = oracle.Graph(300, s, d)
     q = oracle.Query(*QUERIES["diamond"])
     c, h = g.count(q)
     tc, th = 0, 0
     for lo in range(0, 300, 37):
-        a, b = g.count(q, first_range=(lo, min(lo + 37, 300)))
+        a, b = g.count(q, first_range=(lo, min(lo + 37, 300)), mode=mode)
         tc += a
         th = (th + b) & M64
     assert (tc, th) == (c, h)
+
+
+def test_implementation_mode_seeds_are_edges():
+    """Section 4.2: the length-2 prefixes are the edges of the seed atom (filtered by
+    other atoms over the same pair), not the projection-restricted P2 of Fig. 1."""
+    ex_edges = [(0, 1), (1, 2), (2, 0), (3, 0)]  # 0->1 where 1 has out-degree, 3->0 ...
+    g = og(4, ex_edges)
+    q = oracle.Query(*QUERIES["cyclic-triangle"])
+    _, _, st0 = g.count(q, stats=True, mode=0)
+    _, _, st1 = g.count(q, stats=True, mode=1)
+    assert st1.prefixes[2] == 4          # every edge seeds
+    assert st0.prefixes[2] == 3          # (3,0) drops: 3 is not a destination, so not in P1
 
 
 def test_triangle_work_counters():
@@ -237,7 +264,7 @@ def test_triangle_work_counters():
     order a1,a2,a3, every edge is a P2 prefix and proposes min(out(a1), out(a2))."""
     s, d = er_edges(500, 6000, seed=4)
     g = oracle.Graph(500, s, d)
-    c, h, st = g.count(oracle.Query(*QUERIES["triangle"]), stats=True)
+    c, h, st = g.count(oracle.Query(*QUERIES["triangle"]), stats=True, mode=1)
     dout = np.bincount(s, minlength=500)
     assert st.extended[2] == 6000
     assert st.nbind_sum[2] == 2 * 6000
