@@ -1,0 +1,191 @@
+/*
+ * gj.h -- C ABI of libgj, a single-GPU (B300, sm_103a) implementation of the
+ * worst-case optimal Generic Join prefix-extension step and its delta-query
+ * form, after "Distributed Evaluation of Subgraph Queries Using Worst-case
+ * Optimal Low-Memory Dataflows" (Ammar, McSherry, Salihoglu, Joglekar).
+ *
+ * Problem statement (Section 1, Section 2.1): a subgraph query over a
+ * directed graph is a multiway self-join of the edge relation,
+ *     Q(a_0, ..., a_{k-1}) := E(a_s1, a_d1), ..., E(a_sn, a_dn),
+ * evaluated under join (homomorphism) semantics: a match is any assignment
+ * of vertex ids to the attributes such that every atom is an edge. Generic
+ * Join (Fig. 1, Section 2.2) fixes a global attribute order and extends
+ * prefixes one attribute at a time: for each prefix, every atom binding the
+ * next attribute gives an extension set (count), the smallest set proposes
+ * candidates (propose), and each candidate is kept only if it is in all the
+ * other sets (intersect).
+ *
+ * Conventions for every call:
+ *   - Return value: GJ_OK (0) or a negative GJ_E_* code; gj_strerror() names
+ *     it and gj_last_error() gives the context's last message. On error no
+ *     output argument is written unless stated.
+ *   - Vertex ids are uint32 in [0, num_vertices). Match counts are exact
+ *     int64; checksums are uint64 sums modulo 2^64.
+ *   - Input arrays are owned by the caller and are copied (or fully
+ *     consumed) before the call returns; they may be host or device
+ *     pointers (the library asks the CUDA runtime which). Output arrays are
+ *     owned by the caller and must be host memory.
+ *   - Handles (gj_ctx, gj_graph, gj_query) are owned by the library and
+ *     released by their *_free / gj_destroy call.
+ *   - A context and the graphs and queries made from it are used by one host
+ *     thread at a time.
+ *
+ * Match checksum (not from the paper; fixed by this library so that listed
+ * matches can be compared without sorting): H(x) = m(...m(m(m(k) ^ x_0) ^
+ * x_1)... ^ x_{k-1}), the tuple in query attribute order, with m the
+ * SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014); the checksum
+ * of a set of matches is the sum of H over it modulo 2^64. Delta checksums
+ * add H for gained matches and subtract it for lost ones.
+ */
+#ifndef GJ_H
+#define GJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    GJ_OK = 0,
+    GJ_E_INVALID = -1,    /* null pointer, malformed query, bad sign, bad option */
+    GJ_E_RANGE = -2,      /* vertex id >= num_vertices */
+    GJ_E_NOMEM = -3,      /* device or host allocation failed */
+    GJ_E_ADMIT = -4,      /* request needs more device memory than the budget allows */
+    GJ_E_TRUNCATED = -5,  /* more matches than the output capacity */
+    GJ_E_TIMEOUT = -6,    /* a bounded wait expired */
+    GJ_E_OVERFLOW = -7,   /* a count left the int64 range */
+    GJ_E_CUDA = -8,       /* a CUDA runtime call failed (gj_last_error has the text) */
+    GJ_E_PENDING = -9,    /* request not finished yet */
+    GJ_E_NOTFOUND = -10   /* unknown request id */
+};
+
+typedef struct gj_ctx gj_ctx;
+typedef struct gj_graph gj_graph;
+typedef struct gj_query gj_query;
+
+/* Engines for gj_count_ex / gj_count_many. */
+enum {
+    /* Level-synchronous evaluation: separate count, scan, propose+intersect
+     * kernels per level over bounded prefix buffers, the host choosing the
+     * deepest level with pending work after every launch (Section 3.1.1,
+     * Section 3.2; the "plain" one-query-at-a-time path). */
+    GJ_ENGINE_PLAIN = 0,
+    /* One fused launch per call: each warp extends a bounded batch of
+     * prefixes depth-first through all levels (the batching rule of
+     * Section 3.1.2 with B' = one warp's batch), warps take seed ranges from
+     * a shared work counter. */
+    GJ_ENGINE_FUSED = 1
+};
+
+typedef struct {
+    uint64_t prefix_buffer_bytes; /* cap on device prefix buffers of one evaluation; 0 = 512 MiB */
+    uint64_t window;              /* plain engine: candidates per propose+intersect launch; 0 = from the cap */
+    uint32_t engine;              /* default engine of gj_count (GJ_ENGINE_*) */
+    uint32_t flags;               /* reserved, 0 */
+    void* stream;                 /* cudaStream_t for all launches; NULL = the context creates one */
+} gj_options;
+
+/* Units of work of the last gj_count_ex / gj_count_many call on a context,
+ * in the terms of the cost model of Section 2.2 and Theorem 2.1. Index j is
+ * a prefix length; entries j < 2 are zero because evaluation starts from
+ * the length-2 prefixes read off the edges (Section 4.2). */
+typedef struct {
+    int64_t seeds;                /* seed edges read */
+    int64_t extended[9];          /* prefixes of length j that were extended */
+    int64_t nbind[9];             /* sum over those of the number of binding atoms */
+    int64_t proposals[9];         /* sum over those of the smallest extension-set size */
+    int64_t produced[9];          /* prefixes of length j produced (j = k: matches) */
+} gj_work_stats;
+
+/* Creates a context on CUDA device `cuda_device`. opt may be NULL
+ * (defaults). Errors: GJ_E_INVALID (bad device or engine), GJ_E_CUDA. */
+int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out);
+void gj_destroy(gj_ctx* ctx);
+const char* gj_strerror(int code);
+/* Last error message recorded on ctx (empty string if none); valid until the next call. */
+const char* gj_last_error(const gj_ctx* ctx);
+
+/*
+ * Loads the edge relation E from m pairs (src[i], dst[i]) on vertices
+ * [0, num_vertices), host or device arrays. Self-loops are dropped and
+ * duplicate pairs collapse (E is a set, Section 2.1). Builds, on the
+ * device, the forward index (out-neighbours of each vertex, sorted) and
+ * the reverse index (in-neighbours, sorted), the only two indices every
+ * atom shares (Section 4.1). Errors: GJ_E_INVALID (null pointer with m >
+ * 0, num_vertices == 0 or > 2^32 - 1), GJ_E_RANGE, GJ_E_NOMEM, GJ_E_CUDA.
+ */
+int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
+                  gj_graph** out);
+/* Number of distinct edges and the committed version (0 after load, +1 per applied batch). */
+int gj_graph_stats(const gj_graph* g, uint64_t* num_edges, uint64_t* version);
+/* Copies the forward index to host arrays: offsets [num_vertices + 1], neighbours [num_edges]. */
+int gj_graph_export(const gj_graph* g, int64_t* offsets, uint32_t* neighbours);
+void gj_graph_free(gj_graph* g);
+
+/*
+ * Defines Q(a_0..a_{k-1}) := E(a_atoms[0], a_atoms[1]), E(a_atoms[2],
+ * a_atoms[3]), ... with n_atoms atoms, and the global attribute order
+ * `order` (k attribute ids; NULL = 0, 1, ..., k-1). Evaluation starts from
+ * the edges of an atom over the first two attributes of the order, as the
+ * paper's implementation does (Section 4.2), so those two attributes must
+ * share an atom, and every later attribute must share an atom with an
+ * earlier one. Errors: GJ_E_INVALID (k < 2 or > 8, n_atoms > 16, an atom
+ * with equal or out-of-range attributes, order not a permutation, an
+ * attribute in no atom, or the connectivity rule above broken).
+ */
+int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
+                    gj_query** out);
+void gj_query_free(gj_query* q);
+
+/* Count and checksum of the matches of q in the committed graph, default engine. */
+int gj_count(gj_graph* g, const gj_query* q, int64_t* count, uint64_t* checksum);
+
+/*
+ * As gj_count with an explicit engine, restricted to the matches whose first
+ * attribute in the global order has a value in [v_lo, v_hi) (the counts of
+ * disjoint ranges add up). stats may be NULL. Errors: GJ_E_INVALID,
+ * GJ_E_NOMEM, GJ_E_CUDA.
+ */
+int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, uint32_t v_hi, int64_t* count,
+                uint64_t* checksum, gj_work_stats* stats);
+
+/*
+ * Counts nq queries over the committed graph. With GJ_ENGINE_FUSED all of
+ * them run in one persistent launch whose warps share one seed counter (the
+ * batched path); with GJ_ENGINE_PLAIN they run one after another. counts
+ * and checksums are host arrays of nq. Errors: GJ_E_INVALID, GJ_E_NOMEM,
+ * GJ_E_CUDA.
+ */
+int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
+                  uint64_t* checksums);
+
+/* Work units of the last gj_count, gj_count_ex or gj_count_many call on ctx
+ * (summed over queries). */
+int gj_last_work(const gj_ctx* ctx, gj_work_stats* out);
+
+/*
+ * Lists matches: writes up to cap tuples (k uint32 each, query attribute
+ * order, in no particular tuple order) to host memory out_tuples, the
+ * number written to *written, the total to *total and the checksum of all
+ * matches to *checksum. Returns GJ_E_TRUNCATED (outputs still written) if
+ * total > cap.
+ */
+int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, uint64_t* written, int64_t* total,
+            uint64_t* checksum);
+
+/* Kernel timing: when enabled, the launches of the dominant kernel of each
+ * count call are bracketed by CUDA events on the context's stream and their
+ * durations summed. gj_profile_read returns and clears the totals. */
+int gj_profile_enable(gj_ctx* ctx, int enabled);
+int gj_profile_read(gj_ctx* ctx, double* total_ms, uint64_t* launches);
+/* The cudaStream_t all launches of ctx go to. */
+void* gj_ctx_stream(gj_ctx* ctx);
+/* Waits for all work on ctx's stream. */
+int gj_sync(gj_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GJ_H */

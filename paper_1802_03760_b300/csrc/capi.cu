@@ -1,0 +1,355 @@
+// C ABI entry points of libgj (declared and documented in include/gj.h):
+// context, graph and query handles, counting, listing and kernel timing.
+#include "gj_internal.cuh"
+
+#include <new>
+
+void gj_set_error(gj_ctx* ctx, int code, const std::string& msg) {
+    (void)code;
+    if (ctx) ctx->last_error = msg;
+}
+
+int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out) {
+    ScratchArena& a = ctx->scratch[slot];
+    if (a.bytes < bytes) {
+        if (a.ptr) {
+            GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            cudaFree(a.ptr);
+            a.ptr = nullptr;
+            a.bytes = 0;
+        }
+        size_t want = bytes + bytes / 8;
+        GJ_CUDA_TRY(ctx, cudaMalloc(&a.ptr, want));
+        a.bytes = want;
+    }
+    *out = a.ptr;
+    return GJ_OK;
+}
+
+void gj_timer_begin(gj_ctx* ctx) {
+    KernelTimer& t = ctx->timer;
+    if (!t.enabled) return;
+    cudaEvent_t e;
+    if (!t.pool.empty()) {
+        e = t.pool.back();
+        t.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, ctx->stream);
+    t.pending.push_back(e);
+}
+
+void gj_timer_end(gj_ctx* ctx) {
+    KernelTimer& t = ctx->timer;
+    if (!t.enabled || t.pending.size() % 2 == 0) return;
+    cudaEvent_t e;
+    if (!t.pool.empty()) {
+        e = t.pool.back();
+        t.pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        return;
+    }
+    cudaEventRecord(e, ctx->stream);
+    t.pending.push_back(e);
+}
+
+int gj_timer_collect(gj_ctx* ctx) {
+    KernelTimer& t = ctx->timer;
+    if (t.pending.empty()) return GJ_OK;
+    size_t n = t.pending.size() & ~(size_t)1;
+    if (n) GJ_CUDA_TRY(ctx, cudaEventSynchronize(t.pending[n - 1]));
+    for (size_t i = 0; i + 1 < n; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.pending[i], t.pending[i + 1]) == cudaSuccess) {
+            t.total_ms += ms;
+            t.launches++;
+        }
+    }
+    for (cudaEvent_t e : t.pending) t.pool.push_back(e);
+    t.pending.clear();
+    return GJ_OK;
+}
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+struct DevSet {
+    int prev = -1;
+    explicit DevSet(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevSet() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char* gj_strerror(int code) {
+    switch (code) {
+        case GJ_OK: return "ok";
+        case GJ_E_INVALID: return "invalid argument";
+        case GJ_E_RANGE: return "vertex id out of range";
+        case GJ_E_NOMEM: return "out of memory";
+        case GJ_E_ADMIT: return "request exceeds the memory budget";
+        case GJ_E_TRUNCATED: return "output truncated";
+        case GJ_E_TIMEOUT: return "bounded wait expired";
+        case GJ_E_OVERFLOW: return "count overflow";
+        case GJ_E_CUDA: return "CUDA error";
+        case GJ_E_PENDING: return "request pending";
+        case GJ_E_NOTFOUND: return "unknown request";
+        default: return "unknown error";
+    }
+}
+
+const char* gj_last_error(const gj_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
+    if (!out) return GJ_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev) {
+        cudaGetLastError();
+        return cuda_device < 0 ? GJ_E_INVALID : GJ_E_CUDA;
+    }
+    if (opt && opt->engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
+    gj_ctx* ctx = new (std::nothrow) gj_ctx();
+    if (!ctx) return GJ_E_NOMEM;
+    ctx->device = cuda_device;
+    if (opt) ctx->opt = *opt;
+    DevSet ds(cuda_device);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cuda_device);
+    if (ctx->opt.stream) {
+        ctx->stream = (cudaStream_t)ctx->opt.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return GJ_E_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaMalloc(&ctx->d_acc, 64 * sizeof(uint64_t)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_acc, 64 * sizeof(uint64_t)) != cudaSuccess) {
+        gj_destroy(ctx);
+        return GJ_E_NOMEM;
+    }
+    *out = ctx;
+    return GJ_OK;
+}
+
+void gj_destroy(gj_ctx* ctx) {
+    if (!ctx) return;
+    DevSet ds(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& a : ctx->scratch)
+        if (a.ptr) cudaFree(a.ptr);
+    for (cudaEvent_t e : ctx->timer.pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->timer.pending) cudaEventDestroy(e);
+    if (ctx->d_acc) cudaFree(ctx->d_acc);
+    if (ctx->h_acc) cudaFreeHost(ctx->h_acc);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+void* gj_ctx_stream(gj_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
+
+int gj_sync(gj_ctx* ctx) {
+    if (!ctx) return GJ_E_INVALID;
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return GJ_OK;
+}
+
+int gj_profile_enable(gj_ctx* ctx, int enabled) {
+    if (!ctx) return GJ_E_INVALID;
+    ctx->timer.enabled = enabled != 0;
+    return GJ_OK;
+}
+
+int gj_profile_read(gj_ctx* ctx, double* total_ms, uint64_t* launches) {
+    if (!ctx) return GJ_E_INVALID;
+    GJ_TRY(gj_timer_collect(ctx));
+    if (total_ms) *total_ms = ctx->timer.total_ms;
+    if (launches) *launches = ctx->timer.launches;
+    ctx->timer.total_ms = 0;
+    ctx->timer.launches = 0;
+    return GJ_OK;
+}
+
+void gj_graph_free(gj_graph* g) {
+    if (!g) return;
+    DevSet ds(g->ctx->device);
+    cudaStreamSynchronize(g->ctx->stream);
+    for (gj_csr* c : {&g->fwd, &g->rev}) {
+        if (c->off) cudaFree(c->off);
+        if (c->nbr) cudaFree(c->nbr);
+        if (c->key) cudaFree(c->key);
+    }
+    delete g;
+}
+
+int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
+                  gj_graph** out) {
+    if (!ctx || !out || num_vertices == 0 || num_vertices == UINT32_MAX || (m > 0 && (!src || !dst)))
+        return GJ_E_INVALID;
+    *out = nullptr;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    cudaStream_t st = ctx->stream;
+    const uint32_t* ds_ = src;
+    const uint32_t* dd_ = dst;
+    uint32_t* tmp = nullptr;
+    bool dev_s = is_device_ptr(src), dev_d = is_device_ptr(dst);
+    if (m > 0 && (!dev_s || !dev_d)) {
+        GJ_CUDA_TRY(ctx, cudaMallocAsync(&tmp, 2 * m * sizeof(uint32_t), st));
+        if (!dev_s) {
+            GJ_CUDA_TRY(ctx, cudaMemcpyAsync(tmp, src, m * 4, cudaMemcpyHostToDevice, st));
+            ds_ = tmp;
+        }
+        if (!dev_d) {
+            GJ_CUDA_TRY(ctx, cudaMemcpyAsync(tmp + m, dst, m * 4, cudaMemcpyHostToDevice, st));
+            dd_ = tmp + m;
+        }
+    }
+    gj_graph* g = new (std::nothrow) gj_graph();
+    if (!g) return GJ_E_NOMEM;
+    g->ctx = ctx;
+    int rc = gj_csr_build(ctx, ds_, dd_, m, num_vertices, g);
+    if (tmp) cudaFreeAsync(tmp, st);
+    if (rc != GJ_OK) {
+        gj_graph_free(g);
+        return rc;
+    }
+    *out = g;
+    return GJ_OK;
+}
+
+int gj_graph_stats(const gj_graph* g, uint64_t* num_edges, uint64_t* version) {
+    if (!g) return GJ_E_INVALID;
+    if (num_edges) *num_edges = g->m;
+    if (version) *version = g->version;
+    return GJ_OK;
+}
+
+int gj_graph_export(const gj_graph* g, int64_t* offsets, uint32_t* neighbours) {
+    if (!g || !offsets || (!neighbours && g->m)) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    DevSet ds(ctx->device);
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    GJ_CUDA_TRY(ctx, cudaMemcpy(offsets, g->fwd.off, sizeof(int64_t) * ((size_t)g->n + 1), cudaMemcpyDeviceToHost));
+    if (g->m) GJ_CUDA_TRY(ctx, cudaMemcpy(neighbours, g->fwd.nbr, sizeof(uint32_t) * g->m, cudaMemcpyDeviceToHost));
+    return GJ_OK;
+}
+
+int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
+                    gj_query** out) {
+    if (!ctx || !atoms || !out) return GJ_E_INVALID;
+    *out = nullptr;
+    if (n_atoms > GJ_MAX_ATOMS || k > GJ_MAX_K) {
+        gj_set_error(ctx, GJ_E_INVALID, "k > 8 or n_atoms > 16");
+        return GJ_E_INVALID;
+    }
+    gj_query* q = new (std::nothrow) gj_query();
+    if (!q) return GJ_E_NOMEM;
+    q->ctx = ctx;
+    q->k = k;
+    q->natoms = n_atoms;
+    for (uint32_t t = 0; t < n_atoms; t++) {
+        q->as[t] = atoms[2 * t];
+        q->ad[t] = atoms[2 * t + 1];
+    }
+    std::string why;
+    int rc = gj_plan_compile(q->as, q->ad, n_atoms, k, order, &q->plan, &why);
+    if (rc != GJ_OK) {
+        gj_set_error(ctx, rc, "query: " + why);
+        delete q;
+        return rc;
+    }
+    for (uint32_t j = 0; j < k; j++) q->order[j] = q->plan.order[j];
+    *out = q;
+    return GJ_OK;
+}
+
+void gj_query_free(gj_query* q) { delete q; }
+
+int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, uint32_t v_hi, int64_t* count,
+                uint64_t* checksum, gj_work_stats* stats) {
+    if (!g || !q || !count || !checksum || q->ctx != g->ctx || engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int rc;
+    if (engine == GJ_ENGINE_PLAIN)
+        rc = gj_engine_plain(ctx, g, q, v_lo, v_hi, count, checksum, nullptr, 0, nullptr);
+    else
+        rc = gj_engine_fused(ctx, g, &q, 1, v_lo, v_hi, count, checksum);
+    if (rc == GJ_OK && stats) *stats = ctx->work;
+    return rc;
+}
+
+int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
+                  uint64_t* checksums) {
+    if (!g || (nq && (!qs || !counts || !checksums)) || engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
+    for (uint32_t i = 0; i < nq; i++)
+        if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, 0, UINT32_MAX, counts, checksums);
+    gj_work_stats sum{};
+    for (uint32_t i = 0; i < nq; i++) {
+        GJ_TRY(gj_engine_plain(ctx, g, qs[i], 0, UINT32_MAX, counts + i, checksums + i, nullptr, 0, nullptr));
+        const gj_work_stats& w = ctx->work;
+        sum.seeds += w.seeds;
+        for (int j = 0; j < 9; j++) {
+            sum.extended[j] += w.extended[j];
+            sum.nbind[j] += w.nbind[j];
+            sum.proposals[j] += w.proposals[j];
+            sum.produced[j] += w.produced[j];
+        }
+    }
+    ctx->work = sum;
+    return GJ_OK;
+}
+
+int gj_last_work(const gj_ctx* ctx, gj_work_stats* out) {
+    if (!ctx || !out) return GJ_E_INVALID;
+    *out = ctx->work;
+    return GJ_OK;
+}
+
+int gj_count(gj_graph* g, const gj_query* q, int64_t* count, uint64_t* checksum) {
+    if (!g) return GJ_E_INVALID;
+    return gj_count_ex(g, q, g->ctx->opt.engine, 0, UINT32_MAX, count, checksum, nullptr);
+}
+
+int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, uint64_t* written, int64_t* total,
+            uint64_t* checksum) {
+    if (!g || !q || !written || !total || !checksum || (cap && !out_tuples) || q->ctx != g->ctx)
+        return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int64_t c = 0;
+    uint64_t h = 0;
+    GJ_TRY(gj_engine_plain(ctx, g, q, 0, UINT32_MAX, &c, &h, out_tuples, cap, written));
+    *total = c;
+    *checksum = h;
+    return (uint64_t)c > cap ? GJ_E_TRUNCATED : GJ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// Fused engine: one persistent launch evaluates one or many queries.
+//
+// Each warp runs the BiGJoin schedule on its own bounded buffers (Section
+// 3.2 with the batching rule of Section 3.1.2, B' = 32 proposals per step):
+// level j holds at most 2B' = 64 prefixes of length j in shared memory (the
+// invariant of Appendix B). When a level has at least B' prefixes, or its
+// parent has no proposals left, the warp extends it: Count gives each
+// prefix its smallest binding list (min-c, min-i), a warp scan lays their
+// candidates on one line, and every step proposes the next 32 candidates
+// (one per lane, several prefixes per step when lists are short), tests
+// each against the other binding lists by binary search, and ballots the
+// survivors into the next level (or counts and hashes them at the last
+// level). The warp always works on the deepest level with pending work,
+// so memory stays O(k * B') per warp. Warps take 32 seed edges at a time
+// from one counter shared by every query of the launch (work stealing).
+#include "gj_internal.cuh"
+
+namespace {
+
+constexpr int FC = 64;          // frontier capacity per level per warp (2 B')
+constexpr int FT = 32;          // B': descend once a level holds this many prefixes
+constexpr int FW = 8;           // warps per block
+constexpr int SEED_CHUNK = 32;  // seeds per grab
+
+struct FusedArgs {
+    GraphView G;
+    const Plan* plans;
+    uint32_t nq;
+    uint32_t kmax;
+    const uint64_t* qbase;      // [nq + 1] start of each query's seed space (multiples of SEED_CHUNK)
+    const int64_t* seed_lo;     // [nq] first seed slot of each query's seed index
+    const int64_t* seed_n;      // [nq] number of seeds
+    unsigned long long* next;   // work counter over the concatenated seed spaces
+    unsigned long long* counts; // [nq]
+    unsigned long long* chks;   // [nq]
+    unsigned long long* stats;  // [5 * 9] extended, nbind, proposals, produced, seeds; may be null
+};
+
+// Shared-memory layout of one warp (identical on host and device): the
+// plan, 3 x 8 scalars (n, cursor, total per level), then per level j >= 2
+// the prefix tuples [j][FC] (column-major), the min-list pointers [FC],
+// the candidate offsets [FC + 1] and the min-i bytes [FC]. Offsets are
+// closed forms so that no per-level table sits in local memory.
+constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
+constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
+constexpr uint32_t SCAL_BYTES = 3 * GJ_MAX_K * 8;
+constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC;  // mptr + cs + minb
+__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j) {
+    // sum over i = 2..j-1 of (FC * i * 4 + LVL_FIXED)
+    return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + LVL_FIXED * (j - 2);
+}
+__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j) { return lvl_base(j); }
+__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j) { return lvl_base(j) + FC * 4 * j; }
+__host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j) { return off_mptr(j) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j) { return off_cs(j) + ALIGN16((FC + 1) * 8); }
+__host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax) {
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : lvl_base(kmax);
+}
+
+__device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
+    if (s && v) atomicAdd(s + which * 9 + j, v);
+}
+
+__global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint32_t lt = gj_lanemask_lt();
+    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes(A.kmax);
+    Plan& P = *reinterpret_cast<Plan*>(ws);
+    uint64_t* n_ = reinterpret_cast<uint64_t*>(ws + PLAN_BYTES);
+    uint64_t* cur_ = n_ + GJ_MAX_K;
+    uint64_t* tot_ = cur_ + GJ_MAX_K;
+    const GraphView& G = A.G;
+    const uint64_t space = A.qbase[A.nq];
+
+    if (lane < GJ_MAX_K) { n_[lane] = 0; cur_[lane] = 0; tot_[lane] = 0; }
+    __syncwarp();
+
+    int cur_q = -1;
+    uint32_t k = 0;
+    unsigned long long cnt = 0, chk = 0;
+    uint64_t pending = ~0ull;  // a grabbed chunk waiting until the warp's buffers drain
+    int depth = 1;             // deepest level being extended; 1 = none (take seeds)
+
+    auto flush_q = [&]() {
+        unsigned long long c = cnt, h = chk;
+        for (int o = 16; o > 0; o >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            h += __shfl_xor_sync(0xffffffffu, h, o);
+        }
+        if (lane == 0 && cur_q >= 0) {
+            if (c) atomicAdd(A.counts + cur_q, c);
+            if (h) atomicAdd(A.chks + cur_q, h);
+        }
+        cnt = 0;
+        chk = 0;
+    };
+
+    // Count step for level j: min-c / min-i per prefix, scan of min-c.
+    auto activate = [&](int j) {
+        const uint32_t nj = (uint32_t)n_[j];
+        uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j));
+        const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j));
+        uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j));
+        uint8_t* minb = ws + off_minb(j);
+        uint64_t len2[2];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            uint32_t i = lane + 32 * h;
+            uint64_t best = 0;
+            if (i < nj) {
+                best = ~0ull;
+                uint32_t bi = 0;
+                const uint32_t* bp = nullptr;
+                for (uint32_t b = 0; b < P.nb[j]; b++) {
+                    uint32_t v = tup[P.bpos[j][b] * FC + i];
+                    const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
+                    int64_t s = __ldg(off + v);
+                    uint64_t len = (uint64_t)(__ldg(off + v + 1) - s);
+                    if (len < best) {
+                        best = len;
+                        bi = b;
+                        bp = (P.bdir[j][b] ? G.rn : G.fn) + s;
+                    }
+                }
+                mptr[i] = bp;
+                minb[i] = (uint8_t)bi;
+            }
+            len2[h] = best;
+        }
+        // inclusive scans of the two halves, then exclusive offsets
+        uint64_t a = len2[0], b = len2[1];
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t ta = __shfl_up_sync(0xffffffffu, a, o);
+            uint64_t tb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) { a += ta; b += tb; }
+        }
+        uint64_t tot_a = __shfl_sync(0xffffffffu, a, 31);
+        b += tot_a;
+        uint64_t total = __shfl_sync(0xffffffffu, b, 31);
+        cs[lane] = a - len2[0];
+        cs[lane + 32] = b - len2[1];
+        if (lane == 0) {
+            cs[FC] = total;
+            cur_[j] = 0;
+            tot_[j] = total;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            stat_add(A.stats, 0, j, nj);
+            stat_add(A.stats, 1, j, (unsigned long long)nj * P.nb[j]);
+            stat_add(A.stats, 2, j, total);
+        }
+    };
+
+    while (true) {
+        if (depth == 1) {
+            // ---------------- take seeds
+            uint64_t g;
+            if (pending != ~0ull) {
+                g = pending;
+                pending = ~0ull;
+            } else {
+                unsigned long long t = 0;
+                if (lane == 0) t = atomicAdd(A.next, (unsigned long long)SEED_CHUNK);
+                g = __shfl_sync(0xffffffffu, t, 0);
+            }
+            if (g >= space) {
+                if (k > 2 && n_[2] > 0) {
+                    activate(2);
+                    depth = 2;
+                    continue;
+                }
+                break;
+            }
+            // query owning this chunk: last q with qbase[q] <= g
+            uint32_t lo = 0, hi = A.nq;
+            while (hi - lo > 1) {
+                uint32_t mid = (lo + hi) >> 1;
+                if (A.qbase[mid] <= g) lo = mid; else hi = mid;
+            }
+            const int q = (int)lo;
+            if (q != cur_q) {
+                if (k > 2 && n_[2] > 0) {  // finish the other query's prefixes first
+                    pending = g;
+                    activate(2);
+                    depth = 2;
+                    continue;
+                }
+                flush_q();
+                cur_q = q;
+                const uint32_t* srcw = reinterpret_cast<const uint32_t*>(A.plans + q);
+                uint32_t* dstw = reinterpret_cast<uint32_t*>(&P);
+                for (uint32_t w = lane; w < sizeof(Plan) / 4; w += 32) dstw[w] = srcw[w];
+                __syncwarp();
+                k = P.k;
+            }
+            const uint64_t s = g - A.qbase[q] + lane;
+            bool keep = (int64_t)s < A.seed_n[q];
+            if (lane == 0) {
+                int64_t left = A.seed_n[q] - (int64_t)(g - A.qbase[q]);
+                stat_add(A.stats, 4, 0, (unsigned long long)(left < SEED_CHUNK ? left : SEED_CHUNK));
+            }
+            uint32_t x0 = 0, x1 = 0;
+            if (keep) {
+                const int64_t e = A.seed_lo[q] + (int64_t)s;
+                x0 = __ldg((P.seed_dir ? G.rk : G.fk) + e);
+                x1 = __ldg((P.seed_dir ? G.rn : G.fn) + e);
+                for (uint32_t f = 0; f < P.nsf && keep; f++) {
+                    uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
+                    int64_t b0 = __ldg(G.fo + u);
+                    keep = gj_contains(G.fn + b0, __ldg(G.fo + u + 1) - b0, w);
+                }
+            }
+            if (k == 2) {
+                if (keep) {
+                    uint64_t h = gj_mix64(2ull);
+                    uint32_t v0 = P.qpos[0] == 0 ? x0 : x1;
+                    uint32_t v1 = P.qpos[1] == 0 ? x0 : x1;
+                    h = gj_mix64(h ^ (uint64_t)v0);
+                    h = gj_mix64(h ^ (uint64_t)v1);
+                    cnt += 1;
+                    chk += h;
+                }
+                continue;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, keep);
+            uint32_t n2 = (uint32_t)n_[2];
+            if (keep) {
+                uint32_t slot = n2 + __popc(mask & lt);
+                uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(2));
+                tup[0 * FC + slot] = x0;
+                tup[1 * FC + slot] = x1;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                n_[2] = n2 + __popc(mask);
+                stat_add(A.stats, 3, 2, __popc(mask));
+            }
+            __syncwarp();
+            if (n_[2] >= FT) {
+                activate(2);
+                depth = 2;
+            }
+            continue;
+        }
+
+        // ---------------- extend level j = depth
+        const int j = depth;
+        const uint64_t cur = cur_[j], tot = tot_[j];
+        if (cur < tot) {
+            const uint32_t nj = (uint32_t)n_[j];
+            const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j));
+            const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j));
+            const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j));
+            const uint8_t* minb = ws + off_minb(j);
+            const uint64_t t = cur + lane;
+            bool keep = t < tot;
+            uint32_t e = 0, i = 0;
+            if (keep) {
+                // prefix owning candidate t: last i with cs[i] <= t
+                uint32_t lo = 0, hi = nj;
+                while (hi - lo > 1) {
+                    uint32_t mid = (lo + hi) >> 1;
+                    if (cs[mid] <= t) lo = mid; else hi = mid;
+                }
+                i = lo;
+                e = __ldg(mptr[i] + (t - cs[i]));
+                const uint32_t b0 = minb[i];
+                for (uint32_t b = 0; b < P.nb[j] && keep; b++) {
+                    if (b == b0) continue;
+                    uint32_t v = tup[P.bpos[j][b] * FC + i];
+                    const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
+                    const uint32_t* nbr = P.bdir[j][b] ? G.rn : G.fn;
+                    int64_t s = __ldg(off + v);
+                    keep = gj_contains(nbr + s, __ldg(off + v + 1) - s, e);
+                }
+            }
+            if (j == (int)k - 1) {
+                if (keep) {
+                    uint64_t h = gj_mix64((uint64_t)k);
+                    for (uint32_t a = 0; a < k; a++) {
+                        uint32_t p = P.qpos[a];
+                        uint32_t val = (p == (uint32_t)j) ? e : tup[p * FC + i];
+                        h = gj_mix64(h ^ (uint64_t)val);
+                    }
+                    cnt += 1;
+                    chk += h;
+                }
+                if (lane == 0) cur_[j] = cur + 32;
+                __syncwarp();
+                continue;
+            }
+            uint32_t mask = __ballot_sync(0xffffffffu, keep);
+            const uint32_t nn = (uint32_t)n_[j + 1];
+            if (keep) {
+                uint32_t slot = nn + __popc(mask & lt);
+                uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(j + 1));
+                for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
+                nt[j * FC + slot] = e;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                n_[j + 1] = nn + __popc(mask);
+                cur_[j] = cur + 32;
+                stat_add(A.stats, 3, j + 1, __popc(mask));
+            }
+            __syncwarp();
+            if (n_[j + 1] >= FT) {
+                activate(j + 1);
+                depth = j + 1;
+            }
+            continue;
+        }
+        // level j has no proposals left
+        if (j + 1 < (int)k && n_[j + 1] > 0) {
+            activate(j + 1);
+            depth = j + 1;
+            continue;
+        }
+        if (lane == 0) n_[j] = 0;
+        __syncwarp();
+        depth = j - 1;
+    }
+    flush_q();
+}
+
+// Seed ranges of each query: slots of the seed index keyed by x0 in [v_lo, v_hi).
+__global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint32_t v_lo, uint32_t v_hi,
+                              int64_t* seed_lo, int64_t* seed_n, uint64_t* qbase) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t base = 0;
+    for (uint32_t q = 0; q < nq; q++) {
+        const int64_t* off = plans[q].seed_dir ? G.ro : G.fo;
+        int64_t a = off[v_lo], b = off[v_hi];
+        seed_lo[q] = a;
+        seed_n[q] = b - a;
+        qbase[q] = base;
+        base += ((uint64_t)(b - a) + SEED_CHUNK - 1) / SEED_CHUNK * SEED_CHUNK;
+    }
+    qbase[nq] = base;
+}
+
+}  // namespace
+
+int gj_fused_smem_bytes(uint32_t kmax) { return (int)(warp_bytes(kmax) * FW); }
+
+int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
+                    uint32_t v_hi, int64_t* counts, uint64_t* checksums) {
+    if (nq == 0) return GJ_OK;
+    cudaStream_t st = ctx->stream;
+    if (v_hi > g->n) v_hi = g->n;
+    if (v_lo > v_hi) v_lo = v_hi;
+    uint32_t kmax = 2;
+    for (uint32_t q = 0; q < nq; q++) kmax = qs[q]->k > kmax ? qs[q]->k : kmax;
+    // device-side arguments in scratch slot 1
+    size_t plan_bytes = ((sizeof(Plan) * nq) + 255) & ~(size_t)255;
+    size_t need = plan_bytes + 8 * (4 * (size_t)nq + 2) + 8 * (2 * (size_t)nq) + 8 * 64 + 1024;
+    char* base = nullptr;
+    GJ_TRY(gj_scratch(ctx, 1, need, (void**)&base));
+    Plan* d_plans = (Plan*)base;
+    int64_t* seed_lo = (int64_t*)(base + plan_bytes);
+    int64_t* seed_n = seed_lo + nq;
+    uint64_t* qbase = (uint64_t*)(seed_n + nq);
+    unsigned long long* counts_d = (unsigned long long*)(qbase + nq + 1);
+    unsigned long long* chks_d = counts_d + nq;
+    unsigned long long* next = chks_d + nq;
+    unsigned long long* stats = next + 1;
+    std::vector<Plan> hp(nq);
+    for (uint32_t q = 0; q < nq; q++) hp[q] = qs[q]->plan;
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp.data(), sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
+    GraphView G = g->view();
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase);
+
+    const int smem = gj_fused_smem_bytes(kmax);
+    static int configured_smem = 0;
+    if (smem > 48 * 1024 && smem > configured_smem) {
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        configured_smem = smem;
+    }
+    int per_sm = 0;
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    gj_timer_begin(ctx);
+    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    gj_timer_end(ctx);
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    std::vector<unsigned long long> h(2 * (size_t)nq + 1 + 45);
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), counts_d, 8 * h.size(), cudaMemcpyDeviceToHost, st));
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    GJ_TRY(gj_timer_collect(ctx));
+    for (uint32_t q = 0; q < nq; q++) {
+        counts[q] = (int64_t)h[q];
+        checksums[q] = h[nq + q];
+    }
+    gj_work_stats& W = ctx->work;
+    memset(&W, 0, sizeof(W));
+    const unsigned long long* s = h.data() + 2 * nq + 1;
+    for (int j = 0; j < 9; j++) {
+        W.extended[j] = (int64_t)s[0 * 9 + j];
+        W.nbind[j] = (int64_t)s[1 * 9 + j];
+        W.proposals[j] = (int64_t)s[2 * 9 + j];
+        W.produced[j] = (int64_t)s[3 * 9 + j];
+    }
+    W.seeds = (int64_t)s[4 * 9 + 0];
+    int64_t total = 0;
+    for (uint32_t q = 0; q < nq; q++) total += counts[q];
+    if (kmax > 0) W.produced[kmax] = total;
+    return GJ_OK;
+}

@@ -1,0 +1,201 @@
+// Internal declarations shared by the CUDA translation units of libgj.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <cstring>
+#include <climits>
+#include <vector>
+#include <mutex>
+
+#include "../../include/gj.h"
+
+#define GJ_MAX_K 8
+#define GJ_MAX_ATOMS 16
+
+// ------------------------------------------------------------------ errors
+
+struct gj_status_error {
+    int code;
+    std::string msg;
+};
+
+void gj_set_error(gj_ctx* ctx, int code, const std::string& msg);
+
+#define GJ_CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            gj_set_error((ctx), GJ_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? GJ_E_NOMEM : GJ_E_CUDA;                \
+        }                                                                                   \
+    } while (0)
+
+#define GJ_TRY(call)              \
+    do {                          \
+        int rc_ = (call);         \
+        if (rc_ != GJ_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------------------ graph
+
+// Adjacency index in CSR form: off[v] .. off[v+1] delimit v's sorted list in
+// nbr; key[e] is the vertex whose list holds slot e (so (key[e], nbr[e]) is
+// an edge of the index, in index order).
+struct gj_csr {
+    int64_t* off = nullptr;   // [n + 1]
+    uint32_t* nbr = nullptr;  // [m]
+    uint32_t* key = nullptr;  // [m]
+};
+
+// Device view of a graph handed to kernels by value.
+struct GraphView {
+    uint32_t n;
+    uint64_t m;
+    const int64_t* __restrict__ fo;
+    const uint32_t* __restrict__ fn;
+    const uint32_t* __restrict__ fk;
+    const int64_t* __restrict__ ro;
+    const uint32_t* __restrict__ rn;
+    const uint32_t* __restrict__ rk;
+};
+
+struct gj_graph {
+    gj_ctx* ctx = nullptr;
+    uint32_t n = 0;
+    uint64_t m = 0;
+    uint64_t version = 0;
+    gj_csr fwd;  // out-neighbours
+    gj_csr rev;  // in-neighbours
+    GraphView view() const {
+        return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key};
+    }
+};
+
+// ------------------------------------------------------------------ plan
+
+// Execution plan of one query. Positions are places in the execution
+// (global attribute) order; x[p] is the value bound at position p.
+struct Plan {
+    uint32_t k;
+    uint32_t natoms;
+    uint32_t qpos[GJ_MAX_K];    // qpos[a] = position of query attribute a (hash in query order)
+    uint32_t order[GJ_MAX_K];   // order[p] = query attribute at position p
+    // Seed: edges of atom seed_atom give (x0, x1). seed_dir 0: the atom is
+    // E(x0, x1), read from the forward index keyed by x0; 1: E(x1, x0),
+    // read from the reverse index keyed by x0.
+    uint32_t seed_atom;
+    uint32_t seed_dir;
+    uint32_t nsf;                     // further atoms over {x0, x1}: membership filters
+    uint8_t sf_dir[GJ_MAX_ATOMS];     // 0: edge x0->x1 must exist, 1: edge x1->x0
+    uint8_t sf_atom[GJ_MAX_ATOMS];
+    // Level p = 2..k-1 extends prefixes of length p by x_p. Binding atom b
+    // gives the list of x[bpos] in the forward index (bdir 0: atom
+    // E(x_bpos, x_p)) or reverse index (bdir 1: atom E(x_p, x_bpos)).
+    uint32_t nb[GJ_MAX_K];
+    uint8_t bpos[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t bdir[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t batom[GJ_MAX_K][GJ_MAX_ATOMS];
+};
+
+struct gj_query {
+    gj_ctx* ctx = nullptr;
+    uint32_t k = 0, natoms = 0;
+    uint32_t as[GJ_MAX_ATOMS], ad[GJ_MAX_ATOMS];
+    uint32_t order[GJ_MAX_K];
+    Plan plan;
+};
+
+int gj_plan_compile(const uint32_t* as, const uint32_t* ad, uint32_t natoms, uint32_t k, const uint32_t* order,
+                    Plan* out, std::string* why);
+
+// ------------------------------------------------------------------ context
+
+struct ScratchArena {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct KernelTimer {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pending;  // start/stop pairs recorded in the current call
+    std::vector<cudaEvent_t> pool;
+    double total_ms = 0.0;
+    uint64_t launches = 0;
+};
+
+struct gj_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    gj_options opt{};
+    int sm_count = 0;
+    ScratchArena scratch[4];
+    KernelTimer timer;
+    uint64_t* d_acc = nullptr;   // small device accumulators (count, checksum, counters)
+    uint64_t* h_acc = nullptr;   // pinned host mirror
+    std::string last_error;
+    std::mutex mu;
+    gj_work_stats work{};        // units processed by the last count call
+};
+
+// Grow-only device scratch buffer `slot` of at least `bytes`.
+int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out);
+
+// Kernel timing (enabled by gj_profile_enable): wrap launches of the
+// dominant kernel.
+void gj_timer_begin(gj_ctx* ctx);
+void gj_timer_end(gj_ctx* ctx);
+int gj_timer_collect(gj_ctx* ctx);
+
+// ------------------------------------------------------------------ host helpers
+
+// Exclusive prefix sum of n values into out[0..n] (out[n] = total), int64.
+int gj_scan_u32(gj_ctx* ctx, const uint32_t* in, int64_t* out, uint64_t n);
+int gj_scan_i64(gj_ctx* ctx, const int64_t* in, int64_t* out, uint64_t n);
+
+// Sorts n 64-bit keys whose significant bits are [0, bits). keys and tmp
+// are n long; the sorted keys end in *result (keys or tmp).
+int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, uint64_t** result);
+
+int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m, uint32_t n, gj_graph* g);
+
+// Engines: count (and checksum) of a query over the matches whose x0 lies in [v_lo, v_hi).
+int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t v_lo, uint32_t v_hi,
+                    int64_t* count, uint64_t* checksum, uint32_t* out_tuples, uint64_t cap, uint64_t* written);
+
+// One launch over nq queries; counts/checksums are host arrays of nq.
+int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
+                    uint32_t v_hi, int64_t* counts, uint64_t* checksums);
+int gj_fused_smem_bytes(uint32_t kmax);
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ uint64_t gj_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+// Membership of e in the sorted list a[0..len): branch-free binary search
+// (the membership property of an extension index, Section 2.2).
+__device__ __forceinline__ bool gj_contains(const uint32_t* __restrict__ a, int64_t len, uint32_t e) {
+    if (len <= 0) return false;
+    const uint32_t* base = a;
+    int64_t n = len;
+    while (n > 1) {
+        int64_t half = n >> 1;
+        base = (__ldg(base + half) <= e) ? base + half : base;
+        n -= half;
+    }
+    return __ldg(base) == e;
+}
+
+__device__ __forceinline__ uint32_t gj_lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+static inline unsigned gj_div_up(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1) / b); }

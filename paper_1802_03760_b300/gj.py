@@ -1,0 +1,263 @@
+"""Thin Python binding of libgj (include/gj.h), argument marshalling only.
+
+Every step of the evaluation runs in the CUDA library; this module converts
+numpy arrays, torch tensors and Python lists to pointers and raises on error
+codes. If ``libgj.so`` has not been built it raises instead of falling back
+to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgj.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "gj.h")
+
+ENGINE_PLAIN = 0
+ENGINE_FUSED = 1
+
+ERRORS = {
+    -1: "GJ_E_INVALID", -2: "GJ_E_RANGE", -3: "GJ_E_NOMEM", -4: "GJ_E_ADMIT", -5: "GJ_E_TRUNCATED",
+    -6: "GJ_E_TIMEOUT", -7: "GJ_E_OVERFLOW", -8: "GJ_E_CUDA", -9: "GJ_E_PENDING", -10: "GJ_E_NOTFOUND",
+}
+
+
+class GJError(RuntimeError):
+    def __init__(self, code: int, msg: str = ""):
+        self.code = code
+        super().__init__("%s (%d)%s" % (ERRORS.get(code, "error"), code, (": " + msg) if msg else ""))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prefix_buffer_bytes", ctypes.c_uint64), ("window", ctypes.c_uint64),
+                ("engine", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+
+
+class WorkStats(ctypes.Structure):
+    _fields_ = [("seeds", ctypes.c_int64), ("extended", ctypes.c_int64 * 9), ("nbind", ctypes.c_int64 * 9),
+                ("proposals", ctypes.c_int64 * 9), ("produced", ctypes.c_int64 * 9)]
+
+    def as_dict(self):
+        return {"seeds": self.seeds, "extended": list(self.extended), "nbind": list(self.nbind),
+                "proposals": list(self.proposals), "produced": list(self.produced)}
+
+
+_lib = None
+
+_VP = ctypes.c_void_p
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+
+_SIGS = {
+    "gj_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Options), ctypes.POINTER(_VP)]),
+    "gj_destroy": (None, [_VP]),
+    "gj_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "gj_last_error": (ctypes.c_char_p, [_VP]),
+    "gj_graph_load": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_VP)]),
+    "gj_graph_stats": (ctypes.c_int, [_VP, _U64P, _U64P]),
+    "gj_graph_export": (ctypes.c_int, [_VP, _I64P, _U32P]),
+    "gj_graph_free": (None, [_VP]),
+    "gj_query_define": (ctypes.c_int, [_VP, ctypes.c_uint32, _U32P, ctypes.c_uint32, _U32P, ctypes.POINTER(_VP)]),
+    "gj_query_free": (None, [_VP]),
+    "gj_count": (ctypes.c_int, [_VP, _VP, _I64P, _U64P]),
+    "gj_count_ex": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P,
+                                   ctypes.POINTER(WorkStats)]),
+    "gj_count_many": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P]),
+    "gj_last_work": (ctypes.c_int, [_VP, ctypes.POINTER(WorkStats)]),
+    "gj_list": (ctypes.c_int, [_VP, _VP, _U32P, ctypes.c_uint64, _U64P, _I64P, _U64P]),
+    "gj_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "gj_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _U64P]),
+    "gj_ctx_stream": (_VP, [_VP]),
+    "gj_sync": (ctypes.c_int, [_VP]),
+}
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/gj.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gj_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib():
+    """The loaded libgj (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libgj.so is not built; run `python -m paper_1802_03760_b300.build` "
+                              "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    """(pointer, keepalive) for a numpy array, a torch tensor (host or device) or None."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.uint32)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _check(rc: int, ctx=None):
+    if rc < 0:
+        msg = ""
+        if ctx is not None and ctx._h:
+            m = lib().gj_last_error(ctx._h)
+            msg = m.decode() if m else ""
+        raise GJError(rc, msg)
+    return rc
+
+
+class Context:
+    def __init__(self, device: int = 0, prefix_buffer_bytes: int = 0, window: int = 0, engine: int = ENGINE_FUSED,
+                 stream=None):
+        self._h = None
+        o = Options(prefix_buffer_bytes, window, engine, 0, ctypes.c_void_p(stream) if stream else None)
+        h = _VP()
+        _check(lib().gj_create(device, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().gj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self) -> int:
+        return lib().gj_ctx_stream(self._h) or 0
+
+    def sync(self):
+        _check(lib().gj_sync(self._h), self)
+
+    def profile(self, enabled: bool = True):
+        _check(lib().gj_profile_enable(self._h, 1 if enabled else 0), self)
+
+    def profile_read(self):
+        ms = ctypes.c_double(0)
+        n = ctypes.c_uint64(0)
+        _check(lib().gj_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)), self)
+        return ms.value, n.value
+
+    def last_work(self) -> WorkStats:
+        w = WorkStats()
+        _check(lib().gj_last_work(self._h, ctypes.byref(w)), self)
+        return w
+
+
+class Graph:
+    def __init__(self, ctx: Context, src, dst, num_vertices: int):
+        self.ctx = ctx
+        self._h = None
+        ps, ks = _ptr(src)
+        pd, kd = _ptr(dst)
+        m = len(src) if src is not None else 0
+        h = _VP()
+        _check(lib().gj_graph_load(ctx._h, ps, pd, m, num_vertices, ctypes.byref(h)), ctx)
+        self._h = h
+        self.n = num_vertices
+
+    def free(self):
+        if self._h:
+            lib().gj_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def stats(self):
+        m = ctypes.c_uint64(0)
+        v = ctypes.c_uint64(0)
+        _check(lib().gj_graph_stats(self._h, ctypes.byref(m), ctypes.byref(v)), self.ctx)
+        return m.value, v.value
+
+    @property
+    def m(self) -> int:
+        return self.stats()[0]
+
+    def export(self):
+        off = np.empty(self.n + 1, np.int64)
+        nbr = np.empty(max(self.m, 1), np.uint32)
+        _check(lib().gj_graph_export(self._h, off.ctypes.data_as(_I64P), nbr.ctypes.data_as(_U32P)), self.ctx)
+        return off, nbr[:self.m]
+
+
+class Query:
+    def __init__(self, ctx: Context, k: int, atoms, order=None):
+        self.ctx = ctx
+        self._h = None
+        self.k = k
+        self.atoms = [tuple(a) for a in atoms]
+        flat = np.array([x for a in self.atoms for x in a], dtype=np.uint32)
+        o = np.array(order, dtype=np.uint32) if order is not None else None
+        h = _VP()
+        _check(lib().gj_query_define(ctx._h, k, flat.ctypes.data_as(_U32P), len(self.atoms),
+                                     o.ctypes.data_as(_U32P) if o is not None else None, ctypes.byref(h)), ctx)
+        self._h = h
+
+    def free(self):
+        if self._h:
+            lib().gj_query_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def count(g: Graph, q: Query, engine: int | None = None, v_range=None, stats: bool = False):
+    c = ctypes.c_int64(0)
+    h = ctypes.c_uint64(0)
+    if engine is None and v_range is None and not stats:
+        _check(lib().gj_count(g._h, q._h, ctypes.byref(c), ctypes.byref(h)), g.ctx)
+        return c.value, h.value
+    lo, hi = v_range if v_range is not None else (0, 0xFFFFFFFF)
+    w = WorkStats()
+    _check(lib().gj_count_ex(g._h, q._h, ENGINE_FUSED if engine is None else engine, lo, hi, ctypes.byref(c),
+                             ctypes.byref(h), ctypes.byref(w)), g.ctx)
+    if stats:
+        return c.value, h.value, w
+    return c.value, h.value
+
+
+def count_many(g: Graph, qs, engine: int = ENGINE_FUSED):
+    n = len(qs)
+    arr = (_VP * n)(*[q._h for q in qs])
+    c = np.zeros(n, np.int64)
+    h = np.zeros(n, np.uint64)
+    _check(lib().gj_count_many(g._h, arr, n, engine, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
+    return [int(x) for x in c], [int(x) for x in h]
+
+
+def list_matches(g: Graph, q: Query, cap: int):
+    out = np.zeros((max(cap, 1), q.k), np.uint32)
+    w = ctypes.c_uint64(0)
+    t = ctypes.c_int64(0)
+    h = ctypes.c_uint64(0)
+    rc = lib().gj_list(g._h, q._h, out.ctypes.data_as(_U32P), cap, ctypes.byref(w), ctypes.byref(t),
+                       ctypes.byref(h))
+    if rc not in (0, -5):
+        _check(rc, g.ctx)
+    return out[:w.value], t.value, h.value, rc == -5
