@@ -1,0 +1,348 @@
+"""Benchmark: static subgraph-query throughput on the R-MAT scale-20 graph.
+
+One step is one pass of the whole static hot path over one synthetic input:
+build the forward and reverse indices from the device-resident edge list
+(sort, dedup, offsets), then count and checksum the triangle, diamond and
+4-clique queries in one persistent launch of the fused engine. ``value`` is
+matches per second over the step (device-resident inputs, CUDA events on the
+library's stream); ``e2e`` is the same metric through the C ABI with pinned
+host inputs, so every step also copies the edge list in and the counts out.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the full workload on its own GPU (replicas,
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+``--impl reference`` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_03760_b300.inputs import QUERIES, rmat_edges  # noqa: E402
+
+SCALE = 20
+BENCH_QUERIES = ["triangle", "diamond", "4-clique"]
+METRIC = "matches/sec (tri, 4-clique, diamond)"
+WORKLOAD = "static triangle+diamond+4-clique count+checksum, R-MAT scale 20 (2^20 vertices, 2^24 samples)"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(w, k: int) -> int:
+    """Bytes of the prefix-extension cost model for one query's work units.
+
+    8 per seed edge (vertex and neighbour), and per prefix of length j with
+    n_j binding atoms and min count c: 4j (prefix) + 16 n_j (two offsets per
+    atom) + 4c (min list) + 4c(n_j - 1) (one probe per proposal per other
+    atom), plus 4(j+1) per prefix produced for a non-final level.
+    """
+    total = 8 * w.seeds
+    for j in range(2, k):
+        if w.extended[j] == 0:
+            continue
+        nb = w.nbind[j] // w.extended[j]
+        total += 4 * j * w.extended[j] + 16 * w.nbind[j] + 4 * w.proposals[j] + 4 * w.proposals[j] * (nb - 1)
+        if j + 1 < k:
+            total += 4 * (j + 1) * w.produced[j + 1]
+    return total
+
+
+def cpu_sample(s, d, n, target_s: float):
+    """Times the CPU oracle (the paper's evaluation order, single thread) on a
+    first-attribute range of the same workload, grown until it takes about
+    target_s seconds. Returns (matches/s, sample description, seconds, matches)."""
+    import oracle
+
+    og = oracle.Graph(n, s, d)
+    qs = [oracle.Query(*QUERIES[nm]) for nm in BENCH_QUERIES]
+    width = 16
+    while True:
+        t0 = time.perf_counter()
+        matches = 0
+        for q in qs:
+            matches += og.count(q, first_range=(0, width), mode=1)[0]
+        el = time.perf_counter() - t0
+        # widen by 2x until one pass takes a third of the target (the work per
+        # vertex range is skewed, so larger jumps overshoot)
+        if el >= target_s / 3 or width >= n:
+            break
+        width = min(n, width * 2)
+    sample = "first attribute in [0, %d) of %d vertices (%.3f%% of the vertex ids), all three queries" % (
+        width, n, 100.0 * width / n)
+    return matches / el, sample, el, matches
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    n = 1 << SCALE
+    s, d = rmat_edges(SCALE, seed=1)
+    per = max(3.0, 45.0 / max(1, args.steps + args.warmup))
+    vals = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        v, sample, el, _ = cpu_sample(s, d, n, per)
+        if i >= args.warmup:
+            vals.append(v)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "matches/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "engine": "cpu oracle (single thread)"},
+            "cpu_baseline": {"value": v, "unit": "matches/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "matches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1802_03760_b300 import gj
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    n = 1 << SCALE
+    s, d = rmat_edges(SCALE, seed=1)
+    stream = torch.cuda.Stream()
+    ctx = gj.Context(local, stream=stream.cuda_stream)
+    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in BENCH_QUERIES]
+    ds = torch.from_numpy(s.view(np.int32)).cuda()
+    dd = torch.from_numpy(d.view(np.int32)).cuda()
+    hs = torch.from_numpy(s.view(np.int32)).pin_memory()
+    hd = torch.from_numpy(d.view(np.int32)).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(src, dst):
+        g = gj.Graph(ctx, src, dst, n)
+        c, h = gj.count_many(g, qs, engine=gj.ENGINE_FUSED)
+        g.free()
+        return c, h
+
+    def timed(src, dst, k):
+        times = []
+        res = None
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            res = step(src, dst)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return times, res
+
+    # warm-up (also fixes the expected counts of the timed steps)
+    for _ in range(args.warmup):
+        ref = step(ds, dd)
+    # per-query work units (untimed) for the roofline's algorithmic bytes
+    g = gj.Graph(ctx, ds, dd, n)
+    abytes = 0
+    for nm, q in zip(BENCH_QUERIES, qs):
+        _, _, w = gj.count(g, q, engine=gj.ENGINE_FUSED, stats=True)
+        abytes += algorithmic_bytes(w, QUERIES[nm][0])
+    m_edges = g.m
+    g.free()
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile(True)
+    ctx.profile_read()
+    l0 = ctx.launches
+    times, res = timed(ds, dd, args.steps)
+    launches = ctx.launches - l0
+    kern_ms, kern_n = ctx.profile_read()
+    ctx.profile(False)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if res != ref:
+        raise RuntimeError("counts changed between steps: %s vs %s" % (res, ref))
+    matches = sum(res[0])
+    step_ms = sum(times) / len(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the C ABI with pinned host inputs
+    e2e_times, res_e2e = timed(hs, hd, args.steps)
+    if res_e2e != ref:
+        raise RuntimeError("end-to-end counts differ from the device-resident run")
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # the plain level-synchronous engine, one query after another, same workload
+    plain = None
+    if not args.no_plain:
+        ptimes = []
+        for _ in range(max(1, args.plain_steps)):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g = gj.Graph(ctx, ds, dd, n)
+            pc, ph = gj.count_many(g, qs, engine=gj.ENGINE_PLAIN)
+            g.free()
+            e1.record(stream)
+            e1.synchronize()
+            if (pc, ph) != ref:
+                raise RuntimeError("plain engine disagrees with the fused engine")
+            ptimes.append(e0.elapsed_time(e1))
+        pms = sum(ptimes) / len(ptimes)
+        plain = {"ms_per_step": pms, "value": matches / (pms / 1e3), "steps": len(ptimes),
+                 "fused_speedup": pms / step_ms}
+
+    if rank != 0:
+        return 0
+    peak, peak_kind = peaks()
+    kern_avg_ms = kern_ms / max(kern_n, 1)
+    achieved = abytes / (kern_avg_ms / 1e3) / 1e9 if kern_avg_ms > 0 else 0.0
+    cpu_v, cpu_sample_desc, _, _ = cpu_sample(s, d, n, args.cpu_seconds)
+    line = {
+        "metric": METRIC,
+        "value": world * matches / (step_ms / 1e3),
+        "unit": "matches/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": step_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "graph_edges": m_edges, "queries": BENCH_QUERIES,
+                   "engine": "fused (one persistent launch for the three queries) after a GPU index build",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "seed": 1},
+        "matches": dict(zip(BENCH_QUERIES, res[0])),
+        "e2e": {"value": world * matches / (e2e_ms / 1e3), "unit": "matches/s",
+                "h2d_bytes_per_step": int(hs.numel() * 4 + hd.numel() * 4),
+                "d2h_bytes_per_step": 16 * len(BENCH_QUERIES), "ms_per_step": e2e_ms},
+        "roofline": {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": abytes, "kernel_ms_per_launch": kern_avg_ms,
+                     "launches": kern_n},
+        "cpu_baseline": {"value": cpu_v, "unit": "matches/s", "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample_desc},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "plain": plain,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

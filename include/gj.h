@@ -26,7 +26,8 @@
  *     pointers (the library asks the CUDA runtime which). Output arrays are
  *     owned by the caller and must be host memory.
  *   - Handles (gj_ctx, gj_graph, gj_query) are owned by the library and
- *     released by their *_free / gj_destroy call.
+ *     released by their *_free / gj_destroy call; free a context's graphs
+ *     and queries before destroying the context.
  *   - A context and the graphs and queries made from it are used by one host
  *     thread at a time.
  *
@@ -179,6 +180,8 @@ int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, 
  * durations summed. gj_profile_read returns and clears the totals. */
 int gj_profile_enable(gj_ctx* ctx, int enabled);
 int gj_profile_read(gj_ctx* ctx, double* total_ms, uint64_t* launches);
+/* Number of kernels the library has launched on ctx since it was created. */
+uint64_t gj_launch_count(const gj_ctx* ctx);
 /* The cudaStream_t all launches of ctx go to. */
 void* gj_ctx_stream(gj_ctx* ctx);
 /* Waits for all work on ctx's stream. */

@@ -168,6 +168,8 @@ void gj_destroy(gj_ctx* ctx) {
 
 void* gj_ctx_stream(gj_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
+uint64_t gj_launch_count(const gj_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
 int gj_sync(gj_ctx* ctx) {
     if (!ctx) return GJ_E_INVALID;
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

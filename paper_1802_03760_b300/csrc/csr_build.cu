@@ -87,10 +87,10 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
                 uint64_t* mu_out, uint64_t* keys, uint64_t* keys2, uint32_t* flag, int64_t* pos, uint32_t* err) {
     cudaStream_t st = ctx->stream;
     int vb = vertex_bits(n);
-    if (m > 0) k_pack<<<grid_for(ctx, m), 256, 0, st>>>(hi, lo, m, n, vb, keys, err);
+    if (m > 0) { k_pack<<<grid_for(ctx, m), 256, 0, st>>>(hi, lo, m, n, vb, keys, err); GJ_LAUNCHED(ctx); }
     uint64_t* sorted = keys;
     GJ_TRY(gj_radix_sort_u64(ctx, keys, keys2, m, 2 * vb, &sorted));
-    if (m > 0) k_first_of_run<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag);
+    if (m > 0) { k_first_of_run<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag); GJ_LAUNCHED(ctx); }
     GJ_TRY(gj_scan_u32(ctx, flag, pos, m));
     int64_t mu = 0;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&mu, pos + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -98,8 +98,12 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->off, sizeof(int64_t) * ((size_t)n + 1)));
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->nbr, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->key, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
-    if (m > 0) k_scatter_unique<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag, pos, vb, out->nbr, out->key);
+    if (m > 0) {
+        k_scatter_unique<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag, pos, vb, out->nbr, out->key);
+        GJ_LAUNCHED(ctx);
+    }
     k_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(out->key, (uint64_t)mu, n, out->off);
+    GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     *mu_out = (uint64_t)mu;
     return GJ_OK;

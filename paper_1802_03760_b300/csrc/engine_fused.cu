@@ -61,6 +61,7 @@ __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j
     if (s && v) atomicAdd(s + which * 9 + j, v);
 }
 
+
 __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -267,14 +268,16 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 }
                 i = lo;
                 e = __ldg(mptr[i] + (t - cs[i]));
+            }
+            if (keep) {
                 const uint32_t b0 = minb[i];
                 for (uint32_t b = 0; b < P.nb[j] && keep; b++) {
                     if (b == b0) continue;
                     uint32_t v = tup[P.bpos[j][b] * FC + i];
                     const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
                     const uint32_t* nbr = P.bdir[j][b] ? G.rn : G.fn;
-                    int64_t s = __ldg(off + v);
-                    keep = gj_contains(nbr + s, __ldg(off + v + 1) - s, e);
+                    int64_t s0 = __ldg(off + v);
+                    keep = gj_contains(nbr + s0, __ldg(off + v + 1) - s0, e);
                 }
             }
             if (j == (int)k - 1) {
@@ -373,6 +376,7 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
     GraphView G = g->view();
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase);
+    GJ_LAUNCHED(ctx);
 
     const int smem = gj_fused_smem_bytes(kmax);
     static int configured_smem = 0;
@@ -386,6 +390,7 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     gj_timer_begin(ctx);
     k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    GJ_LAUNCHED(ctx);
     gj_timer_end(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     std::vector<unsigned long long> h(2 * (size_t)nq + 1 + 45);

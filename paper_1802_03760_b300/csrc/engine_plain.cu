@@ -269,6 +269,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
         if (l.n == 0) return GJ_OK;
         k_count<<<gj_div_up(l.n, PT) < grid ? gj_div_up(l.n, PT) : grid, PT, 0, st>>>(P, G, j, l.cols, l.n, l.cnt,
                                                                                        l.mini);
+        GJ_LAUNCHED(ctx);
         GJ_TRY(gj_scan_u32(ctx, l.cnt, l.coff, l.n));
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&l.total, l.coff + l.n, 8, cudaMemcpyDeviceToHost, st));
         GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -283,6 +284,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
         if (se[1] > se[0]) {
             gj_timer_begin(ctx);
             k_seed<<<grid, PT, 0, st>>>(P, G, se[0], se[1], Cols{}, A, 1, tuples, cap);
+            GJ_LAUNCHED(ctx);
             gj_timer_end(ctx);
         }
     } else {
@@ -297,6 +299,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
                 if ((uint64_t)chunk > capacity) chunk = (int64_t)capacity;
                 GJ_CUDA_TRY(ctx, cudaMemsetAsync(A.n_out, 0, 8, st));
                 k_seed<<<grid, PT, 0, st>>>(P, G, seed_cursor, seed_cursor + chunk, L[2].cols, A, 0, nullptr, 0);
+                GJ_LAUNCHED(ctx);
                 GJ_CUDA_TRY(ctx, cudaGetLastError());
                 seed_cursor += chunk;
                 GJ_TRY(read_u64(A.n_out, &L[2].n));
@@ -309,6 +312,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
                 gj_timer_begin(ctx);
                 k_extend<<<grid, PT, 0, st>>>(P, G, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.total, 1, Cols{}, A,
                                               tuples, cap);
+                GJ_LAUNCHED(ctx);
                 gj_timer_end(ctx);
                 GJ_CUDA_TRY(ctx, cudaGetLastError());
                 l.cursor = l.total;
@@ -319,6 +323,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
             GJ_CUDA_TRY(ctx, cudaMemsetAsync(A.n_out, 0, 8, st));
             k_extend<<<grid, PT, 0, st>>>(P, G, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.cursor + w, 0,
                                           L[jd + 1].cols, A, nullptr, 0);
+            GJ_LAUNCHED(ctx);
             GJ_CUDA_TRY(ctx, cudaGetLastError());
             l.cursor += w;
             GJ_TRY(read_u64(A.n_out, &L[jd + 1].n));

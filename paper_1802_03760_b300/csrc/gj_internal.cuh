@@ -138,7 +138,11 @@ struct gj_ctx {
     std::string last_error;
     std::mutex mu;
     gj_work_stats work{};        // units processed by the last count call
+    uint64_t launches = 0;       // kernels launched on this context (host-side count)
 };
+
+// Counts one kernel launch of ctx (gj_launch_count reports the total).
+#define GJ_LAUNCHED(ctx) ((ctx)->launches++)
 
 // Grow-only device scratch buffer `slot` of at least `bytes`.
 int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out);

@@ -93,8 +93,10 @@ int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, in
     uint64_t* dst = tmp;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, hist, ntiles);
+        GJ_LAUNCHED(ctx);
         GJ_TRY(gj_scan_u32(ctx, hist, off, nh));
         k_rs_scatter<<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, off, ntiles, dst);
+        GJ_LAUNCHED(ctx);
         GJ_CUDA_TRY(ctx, cudaGetLastError());
         uint64_t* t = src;
         src = dst;

@@ -96,6 +96,11 @@ int scan_impl(gj_ctx* ctx, const T* in, int64_t* out, uint64_t n) {
     int64_t* work = nullptr;
     GJ_TRY(gj_scratch(ctx, 3, sizeof(int64_t) * scan_work(n), (void**)&work));
     scan_rec<T>(ctx->stream, in, out, n, work);
+    for (uint64_t m = n;; m = (m + SCAN_TILE - 1) / SCAN_TILE) {  // 1 launch per single-tile level, else 2
+        if (m <= (uint64_t)SCAN_TILE) { GJ_LAUNCHED(ctx); break; }
+        GJ_LAUNCHED(ctx);
+        GJ_LAUNCHED(ctx);
+    }
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     return GJ_OK;
 }

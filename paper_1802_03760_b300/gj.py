@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import weakref
 
 import numpy as np
 
@@ -73,6 +74,7 @@ _SIGS = {
     "gj_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "gj_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _U64P]),
     "gj_ctx_stream": (_VP, [_VP]),
+    "gj_launch_count": (ctypes.c_uint64, [_VP]),
     "gj_sync": (ctypes.c_int, [_VP]),
 }
 
@@ -128,9 +130,12 @@ class Context:
         h = _VP()
         _check(lib().gj_create(device, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+        self._children = weakref.WeakSet()  # graphs and queries, freed before the context
 
     def close(self):
         if self._h:
+            for c in list(self._children):
+                c.free()
             lib().gj_destroy(self._h)
             self._h = None
 
@@ -156,6 +161,10 @@ class Context:
         _check(lib().gj_profile_read(self._h, ctypes.byref(ms), ctypes.byref(n)), self)
         return ms.value, n.value
 
+    @property
+    def launches(self) -> int:
+        return int(lib().gj_launch_count(self._h))
+
     def last_work(self) -> WorkStats:
         w = WorkStats()
         _check(lib().gj_last_work(self._h, ctypes.byref(w)), self)
@@ -173,6 +182,7 @@ class Graph:
         _check(lib().gj_graph_load(ctx._h, ps, pd, m, num_vertices, ctypes.byref(h)), ctx)
         self._h = h
         self.n = num_vertices
+        ctx._children.add(self)
 
     def free(self):
         if self._h:
@@ -214,6 +224,7 @@ class Query:
         _check(lib().gj_query_define(ctx._h, k, flat.ctypes.data_as(_U32P), len(self.atoms),
                                      o.ctypes.data_as(_U32P) if o is not None else None, ctypes.byref(h)), ctx)
         self._h = h
+        ctx._children.add(self)
 
     def free(self):
         if self._h:
