@@ -161,6 +161,28 @@ int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, 
 int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
                   uint64_t* checksums);
 
+/*
+ * gj_count_many with the fused engine, for callers that must not allocate
+ * device memory during the call: for example a host application whose
+ * device memory is entirely owned by another framework's pool, or a
+ * latency-critical loop where cudaMalloc/cudaFree would stall other streams
+ * by synchronizing the device. The paper has no counterpart; this is an
+ * interface convenience of this library.
+ *
+ * g and the queries are created beforehand (gj_graph_load allocates); the
+ * call itself allocates nothing. Its scratch (plans, seed ranges, counters)
+ * is one 64 KiB array in the library's device memory, resident on every GPU
+ * that loads the library until the process exits. The first call on a
+ * device looks up that array's address (cudaGetSymbolAddress) and caches
+ * it, so make the first call on each device before any stream capture.
+ * Every call on a device shares the array: calls that overlap on the GPU
+ * (from different contexts or streams) race and give wrong counts. At most
+ * 64 queries per call (GJ_E_INVALID above that, with a message in
+ * gj_last_error). counts and checksums are host arrays of nq. Errors:
+ * GJ_E_INVALID, GJ_E_CUDA.
+ */
+int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t nq, int64_t* counts, uint64_t* checksums);
+
 /* Work units of the last gj_count, gj_count_ex or gj_count_many call on ctx
  * (summed over queries). */
 int gj_last_work(const gj_ctx* ctx, gj_work_stats* out);

@@ -416,3 +416,126 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     if (kmax > 0) W.produced[kmax] = total;
     return GJ_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Variant of the fused launch that allocates nothing (gj_count_noalloc).
+//
+// The launch's scratch (query plans, seed ranges, per-query counters, the
+// shared work counter and the work units) lives in one file-scope device
+// array instead of cudaMalloc'd memory. Host code cannot use the array's
+// name as a device address, so the address is fetched once per device with
+// cudaGetSymbolAddress and cached. All calls on a device share the array.
+
+namespace {
+
+constexpr uint32_t NOALLOC_MAX_QUERIES = 64;
+constexpr size_t NOALLOC_SCRATCH_BYTES = 64 * 1024;
+constexpr size_t NA_PLANS = 0;
+constexpr size_t NA_SEED_LO = ((sizeof(Plan) * NOALLOC_MAX_QUERIES) + 255) & ~(size_t)255;
+constexpr size_t NA_SEED_N = NA_SEED_LO + 8 * NOALLOC_MAX_QUERIES;
+constexpr size_t NA_QBASE = NA_SEED_N + 8 * NOALLOC_MAX_QUERIES;
+constexpr size_t NA_COUNTS = NA_QBASE + 8 * (NOALLOC_MAX_QUERIES + 1);    // zeroed per call from here on
+constexpr size_t NA_CHKS = NA_COUNTS + 8 * NOALLOC_MAX_QUERIES;
+constexpr size_t NA_NEXT = NA_CHKS + 8 * NOALLOC_MAX_QUERIES;
+constexpr size_t NA_STATS = NA_NEXT + 8;
+constexpr size_t NA_END = NA_STATS + 8 * 45;
+static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "no-allocation scratch too small");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on `dev` (which must be current).
+int noalloc_scratch(gj_ctx* ctx, int dev, unsigned char** out) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        gj_set_error(ctx, GJ_E_INVALID, "gj_count_noalloc: device id out of range");
+        return GJ_E_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            gj_set_error(ctx, GJ_E_CUDA, std::string("gj_count_noalloc: cudaGetSymbolAddress: ") +
+                                             cudaGetErrorString(e));
+            return GJ_E_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (unsigned char*)g_noalloc_addr[dev];
+    return GJ_OK;
+}
+
+int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, int64_t* counts,
+                  uint64_t* checksums) {
+    cudaStream_t st = ctx->stream;
+    unsigned char* base = nullptr;
+    GJ_TRY(noalloc_scratch(ctx, ctx->device, &base));
+    Plan* d_plans = (Plan*)(base + NA_PLANS);
+    int64_t* seed_lo = (int64_t*)(base + NA_SEED_LO);
+    int64_t* seed_n = (int64_t*)(base + NA_SEED_N);
+    uint64_t* qbase = (uint64_t*)(base + NA_QBASE);
+    unsigned long long* counts_d = (unsigned long long*)(base + NA_COUNTS);
+    unsigned long long* chks_d = (unsigned long long*)(base + NA_CHKS);
+    unsigned long long* next = (unsigned long long*)(base + NA_NEXT);
+    unsigned long long* stats = (unsigned long long*)(base + NA_STATS);
+    uint32_t kmax = 2;
+    for (uint32_t q = 0; q < nq; q++) {
+        kmax = qs[q]->k > kmax ? qs[q]->k : kmax;
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans + q, &qs[q]->plan, sizeof(Plan), cudaMemcpyHostToDevice, st));
+    }
+    // the array keeps the previous call's contents: clear the counters this launch adds into
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(base + NA_COUNTS, 0, NA_END - NA_COUNTS, st));
+    GraphView G = g->view();
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, g->n, seed_lo, seed_n, qbase);
+    GJ_LAUNCHED(ctx);
+    const int smem = gj_fused_smem_bytes(kmax);
+    if (smem > 48 * 1024)
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    GJ_LAUNCHED(ctx);
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    static_assert(sizeof(int64_t) == sizeof(unsigned long long), "count width");
+    unsigned long long hs[45];
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(counts, counts_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(checksums, chks_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    gj_work_stats& W = ctx->work;
+    memset(&W, 0, sizeof(W));
+    for (int j = 0; j < 9; j++) {
+        W.extended[j] = (int64_t)hs[0 * 9 + j];
+        W.nbind[j] = (int64_t)hs[1 * 9 + j];
+        W.proposals[j] = (int64_t)hs[2 * 9 + j];
+        W.produced[j] = (int64_t)hs[3 * 9 + j];
+    }
+    W.seeds = (int64_t)hs[4 * 9 + 0];
+    return GJ_OK;
+}
+
+}  // namespace
+
+extern "C" int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t nq, int64_t* counts,
+                                uint64_t* checksums) {
+    if (!g || !qs || !counts || !checksums || nq == 0) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    if (nq > NOALLOC_MAX_QUERIES) {
+        gj_set_error(ctx, GJ_E_INVALID, "gj_count_noalloc: at most 64 queries per call");
+        return GJ_E_INVALID;
+    }
+    for (uint32_t i = 0; i < nq; i++)
+        if (!qs[i] || qs[i]->ctx != ctx) return GJ_E_INVALID;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    int rc = count_noalloc(ctx, g, qs, nq, counts, checksums);
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return rc;
+}

@@ -69,6 +69,7 @@ _SIGS = {
     "gj_count_ex": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P,
                                    ctypes.POINTER(WorkStats)]),
     "gj_count_many": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P]),
+    "gj_count_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, _I64P, _U64P]),
     "gj_last_work": (ctypes.c_int, [_VP, ctypes.POINTER(WorkStats)]),
     "gj_list": (ctypes.c_int, [_VP, _VP, _U32P, ctypes.c_uint64, _U64P, _I64P, _U64P]),
     "gj_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
@@ -260,6 +261,16 @@ def count_many(g: Graph, qs, engine: int = ENGINE_FUSED):
     h = np.zeros(n, np.uint64)
     _check(lib().gj_count_many(g._h, arr, n, engine, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
     return [int(x) for x in c], [int(x) for x in h]
+
+
+def count_noalloc(g: Graph, qs):
+    """gj_count_noalloc: the fused multi-query count without any device allocation in the call."""
+    n = len(qs)
+    arr = (_VP * n)(*[q._h for q in qs])
+    c = np.zeros(max(n, 1), np.int64)
+    h = np.zeros(max(n, 1), np.uint64)
+    _check(lib().gj_count_noalloc(g._h, arr, n, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
+    return [int(x) for x in c[:n]], [int(x) for x in h[:n]]
 
 
 def list_matches(g: Graph, q: Query, cap: int):
