@@ -35,7 +35,11 @@ from paper_1802_03760_b300.inputs import QUERIES, rmat_edges  # noqa: E402
 SCALE = 20
 BENCH_QUERIES = ["triangle", "diamond", "4-clique"]
 METRIC = "matches/sec (tri, 4-clique, diamond)"
-WORKLOAD = "static triangle+diamond+4-clique count+checksum, R-MAT scale 20 (2^20 vertices, 2^24 samples)"
+
+
+def workload_name(scale, queries):
+    return "static %s count+checksum, R-MAT scale %d (2^%d vertices, 2^%d samples)" % (
+        "+".join(queries), scale, scale, scale + 4)
 
 
 def peaks():
@@ -115,14 +119,14 @@ def algorithmic_bytes(w, k: int) -> int:
     return total
 
 
-def cpu_sample(s, d, n, target_s: float):
+def cpu_sample(s, d, n, target_s: float, queries):
     """Times the CPU oracle (the paper's evaluation order, single thread) on a
     first-attribute range of the same workload, grown until it takes about
     target_s seconds. Returns (matches/s, sample description, seconds, matches)."""
     import oracle
 
     og = oracle.Graph(n, s, d)
-    qs = [oracle.Query(*QUERIES[nm]) for nm in BENCH_QUERIES]
+    qs = [oracle.Query(*QUERIES[nm]) for nm in queries]
     width = 16
     while True:
         t0 = time.perf_counter()
@@ -135,8 +139,8 @@ def cpu_sample(s, d, n, target_s: float):
         if el >= target_s / 3 or width >= n:
             break
         width = min(n, width * 2)
-    sample = "first attribute in [0, %d) of %d vertices (%.3f%% of the vertex ids), all three queries" % (
-        width, n, 100.0 * width / n)
+    sample = "first attribute in [0, %d) of %d vertices (%.3f%% of the vertex ids), queries %s" % (
+        width, n, 100.0 * width / n, "+".join(queries))
     return matches / el, sample, el, matches
 
 
@@ -151,20 +155,20 @@ def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    n = 1 << SCALE
-    s, d = rmat_edges(SCALE, seed=1)
+    n = 1 << args.scale
+    s, d = rmat_edges(args.scale, seed=1)
     per = max(3.0, 45.0 / max(1, args.steps + args.warmup))
     vals = []
     sample = ""
     for i in range(args.warmup + args.steps):
-        v, sample, el, _ = cpu_sample(s, d, n, per)
+        v, sample, el, _ = cpu_sample(s, d, n, per, args.queries)
         if i >= args.warmup:
             vals.append(v)
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "matches/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "engine": "cpu oracle (single thread)"},
+            "config": {"workload": workload_name(args.scale, args.queries), "engine": "cpu oracle (single thread)"},
             "cpu_baseline": {"value": v, "unit": "matches/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": "matches/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -180,11 +184,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
-    n = 1 << SCALE
-    s, d = rmat_edges(SCALE, seed=1)
+    n = 1 << args.scale
+    s, d = rmat_edges(args.scale, seed=1)
     stream = torch.cuda.Stream()
     ctx = gj.Context(local, stream=stream.cuda_stream)
-    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in BENCH_QUERIES]
+    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in args.queries]
     ds = torch.from_numpy(s.view(np.int32)).cuda()
     dd = torch.from_numpy(d.view(np.int32)).cuda()
     hs = torch.from_numpy(s.view(np.int32)).pin_memory()
@@ -219,7 +223,7 @@ def run_ours(args):
     # per-query work units (untimed) for the roofline's algorithmic bytes
     g = gj.Graph(ctx, ds, dd, n)
     abytes = 0
-    for nm, q in zip(BENCH_QUERIES, qs):
+    for nm, q in zip(args.queries, qs):
         _, _, w = gj.count(g, q, engine=gj.ENGINE_FUSED, stats=True)
         abytes += algorithmic_bytes(w, QUERIES[nm][0])
     m_edges = g.m
@@ -290,7 +294,11 @@ def run_ours(args):
     peak, peak_kind = peaks()
     kern_avg_ms = kern_ms / max(kern_n, 1)
     achieved = abytes / (kern_avg_ms / 1e3) / 1e9 if kern_avg_ms > 0 else 0.0
-    cpu_v, cpu_sample_desc, _, _ = cpu_sample(s, d, n, args.cpu_seconds)
+    if args.cpu_seconds > 0:
+        cpu_v, cpu_sample_desc, _, _ = cpu_sample(s, d, n, args.cpu_seconds, args.queries)
+        cpu = {"value": cpu_v, "unit": "matches/s", "cores": 1, "kind": "oracle", "sample": cpu_sample_desc}
+    else:
+        cpu = None
     line = {
         "metric": METRIC,
         "value": world * matches / (step_ms / 1e3),
@@ -304,20 +312,20 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "u32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "graph_edges": m_edges, "queries": BENCH_QUERIES,
+        "config": {"workload": workload_name(args.scale, args.queries), "graph_edges": m_edges,
+                   "queries": args.queries,
                    "engine": "fused (one persistent launch for the three queries) after a GPU index build",
                    "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "seed": 1},
-        "matches": dict(zip(BENCH_QUERIES, res[0])),
+        "matches": dict(zip(args.queries, res[0])),
         "e2e": {"value": world * matches / (e2e_ms / 1e3), "unit": "matches/s",
                 "h2d_bytes_per_step": int(hs.numel() * 4 + hd.numel() * 4),
-                "d2h_bytes_per_step": 16 * len(BENCH_QUERIES), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": 16 * len(args.queries), "ms_per_step": e2e_ms},
         "roofline": {"bound": "hbm", "kernel": "k_fused", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_launch": abytes, "kernel_ms_per_launch": kern_avg_ms,
                      "launches": kern_n},
-        "cpu_baseline": {"value": cpu_v, "unit": "matches/s", "cores": 1, "kind": "oracle",
-                         "sample": cpu_sample_desc},
+        "cpu_baseline": cpu,
         "clocks": clk,
         "gpu_launches": launches,
         "plain": plain,
@@ -332,13 +340,19 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="0 skips the CPU baseline")
+    ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (profiling runs use smaller ones)")
+    ap.add_argument("--queries", default=",".join(BENCH_QUERIES))
     args = ap.parse_args()
+    args.queries = [q for q in args.queries.split(",") if q]
+    for q in args.queries:
+        if q not in QUERIES:
+            ap.error("unknown query %r" % q)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
