@@ -37,14 +37,15 @@ struct FusedArgs {
 };
 
 // Shared-memory layout of one warp (identical on host and device): the
-// plan, 3 x 8 scalars (n, cursor, total per level), then per level j >= 2
-// the prefix tuples [j][FC] (column-major), the min-list pointers [FC],
-// the candidate offsets [FC + 1] and the min-i bytes [FC]. Offsets are
-// closed forms so that no per-level table sits in local memory.
+// plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), then
+// per level j >= 2 the prefix tuples [j][FC] (column-major), the min-list
+// pointers [FC], the candidate offsets [FC + 1], the hash prefixes [FC] and
+// the min-i bytes [FC]. Offsets are closed forms so that no per-level table
+// sits in local memory.
 constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
-constexpr uint32_t SCAL_BYTES = 3 * GJ_MAX_K * 8;
-constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC;  // mptr + cs + minb
+constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
+constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC;  // mptr + cs + hpre + minb
 __host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j) {
     // sum over i = 2..j-1 of (FC * i * 4 + LVL_FIXED)
     return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + LVL_FIXED * (j - 2);
@@ -52,7 +53,8 @@ __host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j) {
 __host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j) { return lvl_base(j); }
 __host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j) { return lvl_base(j) + FC * 4 * j; }
 __host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j) { return off_mptr(j) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j) { return off_cs(j) + ALIGN16((FC + 1) * 8); }
+__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j) { return off_cs(j) + ALIGN16((FC + 1) * 8); }
+__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j) { return off_hpre(j) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax) {
     return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : lvl_base(kmax);
 }
@@ -61,6 +63,21 @@ __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j
     if (s && v) atomicAdd(s + which * 9 + j, v);
 }
 
+
+// Membership of e in the sorted list a[0, len), len < 2^32: branch-free
+// binary search over power-of-two steps (1 + floor(log2 len) probes). The
+// first probe decides whether the answer lies in the top S = 2^floor(log2
+// len) elements; every later probe halves a power-of-two range.
+__device__ __forceinline__ bool member32(const uint32_t* __restrict__ a, uint32_t len, uint32_t e) {
+    if (len == 0) return false;
+    uint32_t step = 1u << (31 - __clz(len));
+    uint32_t pos = (__ldg(a + (len - step)) <= e) ? len - step : 0u;
+    for (step >>= 1; step; step >>= 1) {
+        const uint32_t q = pos + step;
+        pos = (__ldg(a + q) <= e) ? q : pos;
+    }
+    return __ldg(a + pos) == e;
+}
 
 __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -72,39 +89,42 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     uint64_t* n_ = reinterpret_cast<uint64_t*>(ws + PLAN_BYTES);
     uint64_t* cur_ = n_ + GJ_MAX_K;
     uint64_t* tot_ = cur_ + GJ_MAX_K;
+    uint64_t* ip_ = tot_ + GJ_MAX_K;  // prefix that owns candidate cur_ (advances monotonically)
     const GraphView& G = A.G;
     const uint64_t space = A.qbase[A.nq];
 
-    if (lane < GJ_MAX_K) { n_[lane] = 0; cur_[lane] = 0; tot_[lane] = 0; }
+    if (lane < GJ_MAX_K) { n_[lane] = 0; cur_[lane] = 0; tot_[lane] = 0; ip_[lane] = 0; }
     __syncwarp();
 
     int cur_q = -1;
     uint32_t k = 0;
-    unsigned long long cnt = 0, chk = 0;
+    unsigned long long cnt = 0, chk = 0;  // cnt is kept warp-uniform (ballot counts); chk per lane
     uint64_t pending = ~0ull;  // a grabbed chunk waiting until the warp's buffers drain
     int depth = 1;             // deepest level being extended; 1 = none (take seeds)
 
     auto flush_q = [&]() {
-        unsigned long long c = cnt, h = chk;
-        for (int o = 16; o > 0; o >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, o);
-            h += __shfl_xor_sync(0xffffffffu, h, o);
-        }
+        unsigned long long h = chk;
+        for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
         if (lane == 0 && cur_q >= 0) {
-            if (c) atomicAdd(A.counts + cur_q, c);
+            if (cnt) atomicAdd(A.counts + cur_q, cnt);
             if (h) atomicAdd(A.chks + cur_q, h);
         }
         cnt = 0;
         chk = 0;
     };
 
-    // Count step for level j: min-c / min-i per prefix, scan of min-c.
+    // Count step for level j: min-c / min-i per prefix, scan of min-c. At
+    // the last level also the hash of each prefix's attributes that precede
+    // the new one in query order (the tuple hash is a left fold).
     auto activate = [&](int j) {
         const uint32_t nj = (uint32_t)n_[j];
         uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j));
         const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j));
         uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j));
+        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j));
         uint8_t* minb = ws + off_minb(j);
+        const bool last = (j == (int)k - 1);
+        const uint32_t a_new = P.order[j];
         uint64_t len2[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -127,6 +147,11 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 }
                 mptr[i] = bp;
                 minb[i] = (uint8_t)bi;
+                if (last) {
+                    uint64_t hh = gj_mix64((uint64_t)k);
+                    for (uint32_t a = 0; a < a_new; a++) hh = gj_mix64(hh ^ (uint64_t)tup[P.qpos[a] * FC + i]);
+                    hpre[i] = hh;
+                }
             }
             len2[h] = best;
         }
@@ -146,6 +171,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             cs[FC] = total;
             cur_[j] = 0;
             tot_[j] = total;
+            ip_[j] = 0;
         }
         __syncwarp();
         if (lane == 0) {
@@ -211,7 +237,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 for (uint32_t f = 0; f < P.nsf && keep; f++) {
                     uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
                     int64_t b0 = __ldg(G.fo + u);
-                    keep = gj_contains(G.fn + b0, __ldg(G.fo + u + 1) - b0, w);
+                    keep = member32(G.fn + b0, (uint32_t)(__ldg(G.fo + u + 1) - b0), w);
                 }
             }
             if (k == 2) {
@@ -221,9 +247,9 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     uint32_t v1 = P.qpos[1] == 0 ? x0 : x1;
                     h = gj_mix64(h ^ (uint64_t)v0);
                     h = gj_mix64(h ^ (uint64_t)v1);
-                    cnt += 1;
                     chk += h;
                 }
+                cnt += __popc(__ballot_sync(0xffffffffu, keep));
                 continue;
             }
             uint32_t mask = __ballot_sync(0xffffffffu, keep);
@@ -256,42 +282,46 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j));
             const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j));
             const uint8_t* minb = ws + off_minb(j);
+            // the prefix owning candidate cur (warp-uniform, advances monotonically)
+            uint32_t ip = (uint32_t)ip_[j];
+            while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
             const uint64_t t = cur + lane;
             bool keep = t < tot;
-            uint32_t e = 0, i = 0;
-            if (keep) {
-                // prefix owning candidate t: last i with cs[i] <= t
-                uint32_t lo = 0, hi = nj;
+            uint32_t i = ip;
+            if (ip + 1 < nj && cs[ip + 1] < cur + 32) {
+                // this step spans several prefixes: last i with cs[i] <= t
+                uint32_t lo = ip, hi = nj;
                 while (hi - lo > 1) {
                     uint32_t mid = (lo + hi) >> 1;
                     if (cs[mid] <= t) lo = mid; else hi = mid;
                 }
                 i = lo;
-                e = __ldg(mptr[i] + (t - cs[i]));
             }
+            uint32_t e = 0;
             if (keep) {
+                e = __ldg(mptr[i] + (t - cs[i]));
                 const uint32_t b0 = minb[i];
                 for (uint32_t b = 0; b < P.nb[j] && keep; b++) {
                     if (b == b0) continue;
-                    uint32_t v = tup[P.bpos[j][b] * FC + i];
+                    const uint32_t v = tup[P.bpos[j][b] * FC + i];
                     const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
                     const uint32_t* nbr = P.bdir[j][b] ? G.rn : G.fn;
-                    int64_t s0 = __ldg(off + v);
-                    keep = gj_contains(nbr + s0, __ldg(off + v + 1) - s0, e);
+                    const int64_t s0 = __ldg(off + v);
+                    keep = member32(nbr + s0, (uint32_t)(__ldg(off + v + 1) - s0), e);
                 }
             }
             if (j == (int)k - 1) {
                 if (keep) {
-                    uint64_t h = gj_mix64((uint64_t)k);
-                    for (uint32_t a = 0; a < k; a++) {
-                        uint32_t p = P.qpos[a];
-                        uint32_t val = (p == (uint32_t)j) ? e : tup[p * FC + i];
-                        h = gj_mix64(h ^ (uint64_t)val);
-                    }
-                    cnt += 1;
+                    const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j));
+                    uint64_t h = gj_mix64(hpre[i] ^ (uint64_t)e);
+                    for (uint32_t a = P.order[j] + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + i]);
                     chk += h;
                 }
-                if (lane == 0) cur_[j] = cur + 32;
+                cnt += __popc(__ballot_sync(0xffffffffu, keep));
+                if (lane == 0) {
+                    cur_[j] = cur + 32;
+                    ip_[j] = ip;
+                }
                 __syncwarp();
                 continue;
             }
@@ -307,6 +337,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             if (lane == 0) {
                 n_[j + 1] = nn + __popc(mask);
                 cur_[j] = cur + 32;
+                ip_[j] = ip;
                 stat_add(A.stats, 3, j + 1, __popc(mask));
             }
             __syncwarp();
