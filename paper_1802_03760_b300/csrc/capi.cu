@@ -200,6 +200,8 @@ void gj_graph_free(gj_graph* g) {
         if (c->off) cudaFree(c->off);
         if (c->nbr) cudaFree(c->nbr);
         if (c->key) cudaFree(c->key);
+        if (c->tab_off) cudaFree(c->tab_off);
+        if (c->tab) cudaFree(c->tab);
     }
     delete g;
 }

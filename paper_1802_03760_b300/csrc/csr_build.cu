@@ -69,6 +69,38 @@ __global__ void k_offsets(const uint32_t* __restrict__ keyv, uint64_t mu, uint32
     }
 }
 
+// Slot count of each vertex's hash set (0 for lists shorter than GJ_HASH_MIN_DEG).
+__global__ void k_tab_sizes(const int64_t* __restrict__ off, uint32_t n, int64_t* __restrict__ size) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const uint32_t len = (uint32_t)(off[v + 1] - off[v]);
+        size[v] = len >= GJ_HASH_MIN_DEG ? (int64_t)(1ll << gj_tab_bits(len)) : 0;
+    }
+}
+
+// Inserts every neighbour of a long list into its vertex's hash set by
+// linear probing with atomicCAS. A set has at least twice as many slots as
+// distinct keys, so every insertion finds an empty slot.
+__global__ void k_tab_insert(const int64_t* __restrict__ off, const uint32_t* __restrict__ nbr,
+                             const uint32_t* __restrict__ key, uint64_t m, const int64_t* __restrict__ tab_off,
+                             uint32_t* __restrict__ tab) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t v = key[e];
+        const uint32_t len = (uint32_t)(off[v + 1] - off[v]);
+        if (len < GJ_HASH_MIN_DEG) continue;
+        const uint32_t bits = gj_tab_bits(len);
+        const uint32_t mask = (1u << bits) - 1u;
+        uint32_t* t = tab + tab_off[v];
+        const uint32_t x = nbr[e];
+        uint32_t h = gj_tab_home(x, bits);
+        for (uint32_t probe = 0; probe <= mask; probe++) {
+            if (atomicCAS(t + h, GJ_EMPTY, x) == GJ_EMPTY) break;
+            h = (h + 1u) & mask;
+        }
+    }
+}
+
 int vertex_bits(uint32_t n) {
     int b = 1;
     while (b < 32 && (1ull << b) < (uint64_t)n) b++;
@@ -104,6 +136,28 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
     }
     k_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(out->key, (uint64_t)mu, n, out->off);
     GJ_LAUNCHED(ctx);
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    // hash sets of the long lists
+    int64_t* size = nullptr;
+    GJ_CUDA_TRY(ctx, cudaMallocAsync(&size, sizeof(int64_t) * ((size_t)n + 1), st));
+    GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab_off, sizeof(int64_t) * ((size_t)n + 1)));
+    k_tab_sizes<<<grid_for(ctx, n), 256, 0, st>>>(out->off, n, size);
+    GJ_LAUNCHED(ctx);
+    int rc = gj_scan_i64(ctx, size, out->tab_off, n);
+    int64_t tsz = 0;
+    if (rc == GJ_OK) {
+        cudaMemcpyAsync(&tsz, out->tab_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+    }
+    cudaFreeAsync(size, st);
+    GJ_TRY(rc);
+    GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
+    if (tsz > 0) {
+        GJ_CUDA_TRY(ctx, cudaMemsetAsync(out->tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
+        k_tab_insert<<<grid_for(ctx, mu), 256, 0, st>>>(out->off, out->nbr, out->key, (uint64_t)mu, out->tab_off,
+                                                         out->tab);
+        GJ_LAUNCHED(ctx);
+    }
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     *mu_out = (uint64_t)mu;
     return GJ_OK;

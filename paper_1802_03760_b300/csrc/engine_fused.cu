@@ -236,8 +236,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 x1 = __ldg((P.seed_dir ? G.rn : G.fn) + e);
                 for (uint32_t f = 0; f < P.nsf && keep; f++) {
                     uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
-                    int64_t b0 = __ldg(G.fo + u);
-                    keep = member32(G.fn + b0, (uint32_t)(__ldg(G.fo + u + 1) - b0), w);
+                    keep = gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
                 }
             }
             if (k == 2) {
@@ -274,74 +273,119 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
         }
 
         // ---------------- extend level j = depth
+        // Proposals of the level's batch are taken 32 at a time (one per
+        // lane) in a local loop; a mid level leaves the loop as soon as the
+        // next level holds B' prefixes (deepest level first), the last
+        // level runs to the end. When all 32 candidates of a step belong to
+        // one prefix (long lists), that prefix's other binding lists stay
+        // cached in registers across steps.
         const int j = depth;
-        const uint64_t cur = cur_[j], tot = tot_[j];
-        if (cur < tot) {
+        if (cur_[j] < tot_[j]) {
+            const uint64_t tot = tot_[j];
             const uint32_t nj = (uint32_t)n_[j];
             const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j));
             const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j));
             const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j));
+            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j));
             const uint8_t* minb = ws + off_minb(j);
-            // the prefix owning candidate cur (warp-uniform, advances monotonically)
+            const bool last = (j == (int)k - 1);
+            const uint32_t nb = P.nb[j];
+            const uint32_t a_new = P.order[j];
+            uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1));
+            constexpr int MAXO = 3;  // other binding lists cached for a step-uniform prefix
+            const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
+            uint32_t ol[MAXO], obits[MAXO];
+            uint32_t cached = 0xffffffffu;
+            uint64_t cur = cur_[j];
             uint32_t ip = (uint32_t)ip_[j];
-            while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
-            const uint64_t t = cur + lane;
-            bool keep = t < tot;
-            uint32_t i = ip;
-            if (ip + 1 < nj && cs[ip + 1] < cur + 32) {
-                // this step spans several prefixes: last i with cs[i] <= t
-                uint32_t lo = ip, hi = nj;
-                while (hi - lo > 1) {
-                    uint32_t mid = (lo + hi) >> 1;
-                    if (cs[mid] <= t) lo = mid; else hi = mid;
+            uint32_t nn = last ? 0u : (uint32_t)n_[j + 1];
+            bool descend = false;
+            while (cur < tot) {
+                while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
+                const uint64_t t = cur + lane;
+                bool keep = t < tot;
+                const bool uni = !(ip + 1 < nj && cs[ip + 1] < cur + 32);
+                uint32_t i = ip;
+                if (!uni) {
+                    // this step spans several prefixes: last i with cs[i] <= t
+                    uint32_t lo = ip, hi = nj;
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (cs[mid] <= t) lo = mid; else hi = mid;
+                    }
+                    i = lo;
                 }
-                i = lo;
-            }
-            uint32_t e = 0;
-            if (keep) {
-                e = __ldg(mptr[i] + (t - cs[i]));
-                const uint32_t b0 = minb[i];
-                for (uint32_t b = 0; b < P.nb[j] && keep; b++) {
-                    if (b == b0) continue;
-                    const uint32_t v = tup[P.bpos[j][b] * FC + i];
-                    const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
-                    const uint32_t* nbr = P.bdir[j][b] ? G.rn : G.fn;
-                    const int64_t s0 = __ldg(off + v);
-                    keep = member32(nbr + s0, (uint32_t)(__ldg(off + v + 1) - s0), e);
+                uint32_t e = 0;
+                if (keep) e = __ldg(mptr[i] + (t - cs[i]));
+                if (uni && nb - 1 <= (uint32_t)MAXO) {
+                    if (ip != cached) {
+                        const uint32_t b0 = minb[ip];
+                        uint32_t o = 0;
+                        for (uint32_t b = 0; b < nb; b++) {
+                            if (b == b0) continue;
+                            const uint32_t v = tup[P.bpos[j][b] * FC + ip];
+                            const uint32_t dir = P.bdir[j][b];
+                            const int64_t* off = dir ? G.ro : G.fo;
+                            const int64_t s0 = __ldg(off + v);
+                            const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s0);
+                            const bool hashed = len >= GJ_HASH_MIN_DEG;
+                            const uint32_t* p = hashed ? (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v)
+                                                       : (dir ? G.rn : G.fn) + s0;
+#pragma unroll
+                            for (int q = 0; q < MAXO; q++)
+                                if (q == (int)o) {
+                                    ob[q] = p;
+                                    ol[q] = len;
+                                    obits[q] = hashed ? gj_tab_bits(len) : 0u;
+                                }
+                            o++;
+                        }
+                        cached = ip;
+                    }
+#pragma unroll
+                    for (int q = 0; q < MAXO; q++)
+                        if (q + 1 < (int)nb && keep)
+                            keep = obits[q] ? gj_tab_member(ob[q], obits[q], e) : member32(ob[q], ol[q], e);
+                } else if (keep) {
+                    const uint32_t b0 = minb[i];
+                    for (uint32_t b = 0; b < nb && keep; b++) {
+                        if (b == b0) continue;
+                        const uint32_t v = tup[P.bpos[j][b] * FC + i];
+                        keep = P.bdir[j][b] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
+                                            : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
+                    }
                 }
-            }
-            if (j == (int)k - 1) {
+                cur += 32;
+                if (last) {
+                    if (keep) {
+                        uint64_t h = gj_mix64(hpre[i] ^ (uint64_t)e);
+                        for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + i]);
+                        chk += h;
+                    }
+                    cnt += __popc(__ballot_sync(0xffffffffu, keep));
+                    continue;
+                }
+                const uint32_t mask = __ballot_sync(0xffffffffu, keep);
                 if (keep) {
-                    const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j));
-                    uint64_t h = gj_mix64(hpre[i] ^ (uint64_t)e);
-                    for (uint32_t a = P.order[j] + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + i]);
-                    chk += h;
+                    const uint32_t slot = nn + __popc(mask & lt);
+                    for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
+                    nt[j * FC + slot] = e;
                 }
-                cnt += __popc(__ballot_sync(0xffffffffu, keep));
-                if (lane == 0) {
-                    cur_[j] = cur + 32;
-                    ip_[j] = ip;
+                nn += __popc(mask);
+                if (lane == 0) stat_add(A.stats, 3, j + 1, __popc(mask));
+                if (nn >= FT) {
+                    descend = true;
+                    break;
                 }
-                __syncwarp();
-                continue;
-            }
-            uint32_t mask = __ballot_sync(0xffffffffu, keep);
-            const uint32_t nn = (uint32_t)n_[j + 1];
-            if (keep) {
-                uint32_t slot = nn + __popc(mask & lt);
-                uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(j + 1));
-                for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
-                nt[j * FC + slot] = e;
             }
             __syncwarp();
             if (lane == 0) {
-                n_[j + 1] = nn + __popc(mask);
-                cur_[j] = cur + 32;
+                cur_[j] = cur;
                 ip_[j] = ip;
-                stat_add(A.stats, 3, j + 1, __popc(mask));
+                if (!last) n_[j + 1] = nn;
             }
             __syncwarp();
-            if (n_[j + 1] >= FT) {
+            if (descend) {
                 activate(j + 1);
                 depth = j + 1;
             }

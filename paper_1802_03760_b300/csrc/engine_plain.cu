@@ -67,11 +67,8 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, int64_t e_lo, 
             x0 = __ldg(key + e);
             x1 = __ldg(nbr + e);
             for (uint32_t f = 0; f < P.nsf && keep; f++) {
-                const uint32_t* a;
-                int64_t len;
                 uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
-                list_of(G, 0, u, a, len);
-                keep = gj_contains(a, len, w);
+                keep = gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
             }
         }
         if (emit) {
@@ -157,8 +154,9 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, uint32_t j, 
             xs[j] = e;
             for (uint32_t bb = 0; bb < P.nb[j] && keep; bb++) {
                 if (bb == b) continue;
-                list_of(G, P.bdir[j][bb], xs[P.bpos[j][bb]], a, len);
-                keep = gj_contains(a, len, e);
+                const uint32_t v = xs[P.bpos[j][bb]];
+                keep = P.bdir[j][bb] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
+                                     : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
             }
         }
         if (last) {

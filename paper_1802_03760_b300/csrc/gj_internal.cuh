@@ -42,12 +42,19 @@ void gj_set_error(gj_ctx* ctx, int code, const std::string& msg);
 
 // Adjacency index in CSR form: off[v] .. off[v+1] delimit v's sorted list in
 // nbr; key[e] is the vertex whose list holds slot e (so (key[e], nbr[e]) is
-// an edge of the index, in index order).
+// an edge of the index, in index order). Lists of at least GJ_HASH_MIN_DEG
+// entries also get an open-addressing hash set in tab (2^ceil(log2(2 len))
+// slots from tab_off[v], empty slots all ones) for constant-time membership.
 struct gj_csr {
-    int64_t* off = nullptr;   // [n + 1]
-    uint32_t* nbr = nullptr;  // [m]
-    uint32_t* key = nullptr;  // [m]
+    int64_t* off = nullptr;      // [n + 1]
+    uint32_t* nbr = nullptr;     // [m]
+    uint32_t* key = nullptr;     // [m]
+    int64_t* tab_off = nullptr;  // [n + 1]
+    uint32_t* tab = nullptr;     // [tab_off[n]]
 };
+
+constexpr uint32_t GJ_HASH_MIN_DEG = 16;
+constexpr uint32_t GJ_EMPTY = 0xffffffffu;
 
 // Device view of a graph handed to kernels by value.
 struct GraphView {
@@ -59,6 +66,10 @@ struct GraphView {
     const int64_t* __restrict__ ro;
     const uint32_t* __restrict__ rn;
     const uint32_t* __restrict__ rk;
+    const int64_t* __restrict__ fto;  // hash sets of the forward lists
+    const uint32_t* __restrict__ ft;
+    const int64_t* __restrict__ rto;  // hash sets of the reverse lists
+    const uint32_t* __restrict__ rt;
 };
 
 struct gj_graph {
@@ -69,7 +80,8 @@ struct gj_graph {
     gj_csr fwd;  // out-neighbours
     gj_csr rev;  // in-neighbours
     GraphView view() const {
-        return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key};
+        return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
+                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab};
     }
 };
 
@@ -194,6 +206,48 @@ __device__ __forceinline__ bool gj_contains(const uint32_t* __restrict__ a, int6
         n -= half;
     }
     return __ldg(base) == e;
+}
+
+// Slot count exponent of the hash set of a list of len entries:
+// 2^ceil(log2(2 len)) slots, so the load factor stays in (1/4, 1/2].
+__host__ __device__ __forceinline__ uint32_t gj_tab_bits(uint32_t len) {
+#ifdef __CUDA_ARCH__
+    return 32u - __clz(2u * len - 1u);
+#else
+    uint32_t b = 0;
+    while ((1ull << b) < 2ull * len) b++;
+    return b;
+#endif
+}
+
+// Home slot of e in a set of 2^bits slots: multiplicative hashing with
+// the 32-bit golden-ratio constant (Knuth, TAOCP vol. 3, Section 6.4).
+__device__ __forceinline__ uint32_t gj_tab_home(uint32_t e, uint32_t bits) {
+    return (e * 0x9e3779b1u) >> (32u - bits);
+}
+
+// Membership of e in a linear-probing hash set (no deletions, never full):
+// probe from the home slot until e or an empty slot.
+__device__ __forceinline__ bool gj_tab_member(const uint32_t* __restrict__ tab, uint32_t bits, uint32_t e) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h = gj_tab_home(e, bits);
+    while (true) {
+        const uint32_t v = __ldg(tab + h);
+        if (v == e) return true;
+        if (v == GJ_EMPTY) return false;
+        h = (h + 1u) & mask;
+    }
+}
+
+// Membership of e in the list of v in index (off, nbr, tab_off, tab): the
+// hash set for long lists, binary search for short ones.
+__device__ __forceinline__ bool gj_list_member(const int64_t* __restrict__ off, const uint32_t* __restrict__ nbr,
+                                               const int64_t* __restrict__ tab_off, const uint32_t* __restrict__ tab,
+                                               uint32_t v, uint32_t e) {
+    const int64_t s = __ldg(off + v);
+    const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s);
+    if (len >= GJ_HASH_MIN_DEG) return gj_tab_member(tab + __ldg(tab_off + v), gj_tab_bits(len), e);
+    return gj_contains(nbr + s, len, e);
 }
 
 __device__ __forceinline__ uint32_t gj_lanemask_lt() {
