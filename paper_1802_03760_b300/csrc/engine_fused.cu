@@ -79,6 +79,53 @@ __device__ __forceinline__ bool member32(const uint32_t* __restrict__ a, uint32_
     return __ldg(a + pos) == e;
 }
 
+// Two membership tests against the same sorted list, interleaved so that
+// the two chains of dependent loads overlap (same list: same step count).
+__device__ __forceinline__ void member32x2(const uint32_t* __restrict__ a, uint32_t len, uint32_t e0, bool& k0,
+                                           uint32_t e1, bool& k1) {
+    if (len == 0) {
+        k0 = k1 = false;
+        return;
+    }
+    uint32_t step = 1u << (31 - __clz(len));
+    const uint32_t x = __ldg(a + (len - step));
+    uint32_t p0 = (x <= e0) ? len - step : 0u;
+    uint32_t p1 = (x <= e1) ? len - step : 0u;
+    for (step >>= 1; step; step >>= 1) {
+        const uint32_t q0 = p0 + step, q1 = p1 + step;
+        const uint32_t v0 = __ldg(a + q0), v1 = __ldg(a + q1);
+        p0 = (v0 <= e0) ? q0 : p0;
+        p1 = (v1 <= e1) ? q1 : p1;
+    }
+    const uint32_t f0 = __ldg(a + p0), f1 = __ldg(a + p1);
+    k0 = k0 && f0 == e0;
+    k1 = k1 && f1 == e1;
+}
+
+// Two membership tests against the same hash set, probes interleaved.
+__device__ __forceinline__ void tab_member2(const uint32_t* __restrict__ tab, uint32_t bits, uint32_t e0, bool& k0,
+                                            uint32_t e1, bool& k1) {
+    const uint32_t mask = (1u << bits) - 1u;
+    uint32_t h0 = gj_tab_home(e0, bits), h1 = gj_tab_home(e1, bits);
+    bool a0 = k0, a1 = k1, r0 = false, r1 = false;
+    while (a0 || a1) {
+        const uint32_t v0 = a0 ? __ldg(tab + h0) : 0u;
+        const uint32_t v1 = a1 ? __ldg(tab + h1) : 0u;
+        if (a0) {
+            if (v0 == e0) { r0 = true; a0 = false; }
+            else if (v0 == GJ_EMPTY) a0 = false;
+            else h0 = (h0 + 1u) & mask;
+        }
+        if (a1) {
+            if (v1 == e1) { r1 = true; a1 = false; }
+            else if (v1 == GJ_EMPTY) a1 = false;
+            else h1 = (h1 + 1u) & mask;
+        }
+    }
+    k0 = r0;
+    k1 = r1;
+}
+
 __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
@@ -302,6 +349,60 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             bool descend = false;
             while (cur < tot) {
                 while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
+                if (last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
+                    // Last level, next 64 candidates all in prefix ip: two per
+                    // lane, with their probes interleaved.
+                    if (ip != cached) {
+                        const uint32_t b0 = minb[ip];
+                        uint32_t o = 0;
+                        for (uint32_t b = 0; b < nb; b++) {
+                            if (b == b0) continue;
+                            const uint32_t v = tup[P.bpos[j][b] * FC + ip];
+                            const uint32_t dir = P.bdir[j][b];
+                            const int64_t* off = dir ? G.ro : G.fo;
+                            const int64_t s0 = __ldg(off + v);
+                            const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s0);
+                            const bool hashed = len >= GJ_HASH_MIN_DEG;
+                            const uint32_t* p = hashed ? (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v)
+                                                       : (dir ? G.rn : G.fn) + s0;
+#pragma unroll
+                            for (int q = 0; q < MAXO; q++)
+                                if (q == (int)o) {
+                                    ob[q] = p;
+                                    ol[q] = len;
+                                    obits[q] = hashed ? gj_tab_bits(len) : 0u;
+                                }
+                            o++;
+                        }
+                        cached = ip;
+                    }
+                    const uint64_t t0 = cur + lane, t1 = cur + 32 + lane;
+                    bool k0 = t0 < tot, k1 = t1 < tot;
+                    const uint32_t* ml = mptr[ip];
+                    const uint64_t c0 = cs[ip];
+                    const uint32_t e0 = k0 ? __ldg(ml + (t0 - c0)) : 0u;
+                    const uint32_t e1 = k1 ? __ldg(ml + (t1 - c0)) : 0u;
+#pragma unroll
+                    for (int q = 0; q < MAXO; q++) {
+                        if (q + 1 < (int)nb) {
+                            if (obits[q]) tab_member2(ob[q], obits[q], e0, k0, e1, k1);
+                            else member32x2(ob[q], ol[q], e0, k0, e1, k1);
+                        }
+                    }
+                    if (k0 | k1) {
+                        const uint64_t hp = hpre[ip];
+                        uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
+                        for (uint32_t a = a_new + 1; a < k; a++) {
+                            const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
+                            h0 = gj_mix64(h0 ^ x);
+                            h1 = gj_mix64(h1 ^ x);
+                        }
+                        chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
+                    }
+                    cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                    cur += 64;
+                    continue;
+                }
                 const uint64_t t = cur + lane;
                 bool keep = t < tot;
                 const bool uni = !(ip + 1 < nj && cs[ip + 1] < cur + 32);
