@@ -197,6 +197,30 @@ int gj_last_work(const gj_ctx* ctx, gj_work_stats* out);
 int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, uint64_t* written, int64_t* total,
             uint64_t* checksum);
 
+/*
+ * Applies a batch of b signed edge updates (src[i], dst[i], sign[i] = +1
+ * insert / -1 delete; host or device arrays) to g and returns, for each of
+ * the nq queries, the change of its match count and checksum (host arrays
+ * delta_count[nq], delta_checksum[nq]; checksums add H of gained matches
+ * and subtract H of lost ones, mod 2^64).
+ *
+ * Batch semantics (R' = R + Delta R, Section 3.3.1): updates apply in batch
+ * order, so the last update of an edge decides whether it is present
+ * afterwards; self-loops are ignored; an insert of a present edge or a
+ * delete of an absent one changes nothing. The change is computed with the
+ * delta queries dQ_1..dQ_n of Delta-GJ (Section 3.3.1): dQ_i is seeded from
+ * the changed edges under atom i, atoms before i (definition order) read
+ * the new graph and atoms after i the old one (Section 4.3), and the signed
+ * sum over all dQ_i is exactly count(after) - count(before). The batch is
+ * then committed: the version advances and later counts see it. On error
+ * the graph is unchanged. Errors: GJ_E_INVALID (null pointer, sign not +-1,
+ * b >= 2^32), GJ_E_RANGE, GJ_E_NOMEM, GJ_E_CUDA.
+ */
+int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign, uint64_t b,
+                   const gj_query* const* qs, uint32_t nq, int64_t* delta_count, uint64_t* delta_checksum);
+/* Number of edges whose presence the last gj_apply_batch on g changed. */
+int gj_graph_last_batch(const gj_graph* g, uint64_t* changes);
+
 /* Kernel timing: when enabled, the launches of the dominant kernel of each
  * count call are bracketed by CUDA events on the context's stream and their
  * durations summed. gj_profile_read returns and clears the totals. */

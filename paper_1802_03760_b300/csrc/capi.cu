@@ -284,6 +284,14 @@ int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_a
         return rc;
     }
     for (uint32_t j = 0; j < k; j++) q->order[j] = q->plan.order[j];
+    for (uint32_t i = 0; i < n_atoms; i++) {
+        rc = gj_plan_compile_delta(q, i, &q->dplan[i], &why);
+        if (rc != GJ_OK) {
+            gj_set_error(ctx, rc, "query: " + why);
+            delete q;
+            return rc;
+        }
+    }
     *out = q;
     return GJ_OK;
 }
@@ -339,6 +347,57 @@ int gj_last_work(const gj_ctx* ctx, gj_work_stats* out) {
 int gj_count(gj_graph* g, const gj_query* q, int64_t* count, uint64_t* checksum) {
     if (!g) return GJ_E_INVALID;
     return gj_count_ex(g, q, g->ctx->opt.engine, 0, UINT32_MAX, count, checksum, nullptr);
+}
+
+int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign, uint64_t b,
+                   const gj_query* const* qs, uint32_t nq, int64_t* delta_count, uint64_t* delta_checksum) {
+    if (!g || (b && (!src || !dst || !sign)) || (nq && (!qs || !delta_count || !delta_checksum)) || b > UINT32_MAX)
+        return GJ_E_INVALID;
+    for (uint32_t i = 0; i < nq; i++)
+        if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeltaBuf buf;
+    int rc = gj_delta_prepare(ctx, g, src, dst, sign, b, &buf);
+    gj_work_stats sum{};
+    for (uint32_t qi = 0; qi < nq && rc == GJ_OK; qi++) {
+        const gj_query* q = qs[qi];
+        int64_t c = 0;
+        uint64_t h = 0;
+        for (uint32_t i = 0; i < q->natoms && rc == GJ_OK && buf.batch.n; i++) {
+            int64_t ci = 0;
+            uint64_t hi = 0;
+            rc = gj_engine_plain_plan(ctx, g, q->dplan[i], 0, UINT32_MAX, &buf.batch, &ci, &hi, nullptr, 0, nullptr);
+            c += ci;
+            h += hi;
+            const gj_work_stats& w = ctx->work;
+            sum.seeds += w.seeds;
+            for (int j = 0; j < 9; j++) {
+                sum.extended[j] += w.extended[j];
+                sum.nbind[j] += w.nbind[j];
+                sum.proposals[j] += w.proposals[j];
+                sum.produced[j] += w.produced[j];
+            }
+        }
+        delta_count[qi] = c;
+        delta_checksum[qi] = h;
+    }
+    const uint64_t changes = buf.batch.n;
+    if (rc == GJ_OK) rc = gj_delta_commit(ctx, g, buf.batch);
+    gj_delta_free(ctx, &buf);
+    if (rc == GJ_OK) {
+        GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        g->last_changes = changes;
+        ctx->work = sum;
+    }
+    return rc;
+}
+
+int gj_graph_last_batch(const gj_graph* g, uint64_t* changes) {
+    if (!g || !changes) return GJ_E_INVALID;
+    *changes = g->last_changes;
+    return GJ_OK;
 }
 
 int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, uint64_t* written, int64_t* total,

@@ -12,6 +12,10 @@
 // survivors to the next level's buffer (or counts and hashes them at the
 // last level). After each launch the host reads the sizes back and picks
 // the deepest level with pending candidates (Section 3.2).
+//
+// The same kernels evaluate delta queries dQ_i (Section 3.3.1, Section 4.3):
+// the seeds are a batch's signed changes, each atom reads the old or the
+// new version of the graph, and every prefix carries its seed's sign.
 #include "gj_internal.cuh"
 
 namespace {
@@ -20,6 +24,7 @@ constexpr int PT = 256;  // threads per block
 
 struct Cols {
     uint32_t* x[GJ_MAX_K];
+    int8_t* sg;  // sign of the seed each prefix descends from (delta queries)
 };
 
 struct Acc {
@@ -28,15 +33,6 @@ struct Acc {
     unsigned long long* n_out;  // append cursor of the next level's buffer
     unsigned long long* tup;    // slot cursor of listed matches
 };
-
-__device__ __forceinline__ void list_of(const GraphView& G, uint32_t dir, uint32_t v, const uint32_t*& a,
-                                        int64_t& len) {
-    const int64_t* off = dir ? G.ro : G.fo;
-    const uint32_t* nbr = dir ? G.rn : G.fn;
-    int64_t b = __ldg(off + v);
-    len = __ldg(off + v + 1) - b;
-    a = nbr + b;
-}
 
 __device__ __forceinline__ uint64_t hash_positions(const Plan& P, const uint32_t* xs) {
     uint64_t h = gj_mix64((uint64_t)P.k);
@@ -49,12 +45,16 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned long 
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
 }
 
-// Reads seed edges [e_lo, e_hi) of the seed index and keeps those that pass
-// the other atoms over (x0, x1). k == 2 counts them as matches.
-__global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, int64_t e_lo, int64_t e_hi, Cols out, Acc acc,
-                                             int emit, uint32_t* __restrict__ tuples, uint64_t cap) {
+// Reads seeds [e_lo, e_hi) and keeps those that pass the other atoms over
+// (x0, x1). Static plans read the seed atom's index slots; delta plans read
+// the batch's changes (sorted (src, dst) pairs with signs). k == 2 counts
+// the seeds as matches.
+__global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, DeltaView D, DeltaBatch B, int64_t e_lo,
+                                             int64_t e_hi, Cols out, Acc acc, int emit, uint32_t* __restrict__ tuples,
+                                             uint64_t cap) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gj_lanemask_lt();
+    const DeltaView* Dv = P.delta ? &D : nullptr;
     const uint32_t* key = P.seed_dir ? G.rk : G.fk;
     const uint32_t* nbr = P.seed_dir ? G.rn : G.fn;
     unsigned long long cnt = 0, chk = 0;
@@ -63,19 +63,27 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, int64_t e_lo, 
         int64_t e = base + lane;
         bool keep = e < e_hi;
         uint32_t x0 = 0, x1 = 0;
+        int sign = 1;
         if (keep) {
-            x0 = __ldg(key + e);
-            x1 = __ldg(nbr + e);
+            if (P.delta) {
+                x0 = B.chg_src[e];
+                x1 = B.chg_dst[e];
+                sign = B.chg_sign[e];
+            } else {
+                x0 = __ldg(key + e);
+                x1 = __ldg(nbr + e);
+            }
             for (uint32_t f = 0; f < P.nsf && keep; f++) {
                 uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
-                keep = gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
+                keep = gj_view_member(G, Dv, 0, P.sf_view[f], u, w);
             }
         }
         if (emit) {
             if (keep) {
                 uint32_t xs[2] = {x0, x1};
-                cnt += 1;
-                chk += hash_positions(P, xs);
+                const uint64_t h = hash_positions(P, xs);
+                cnt += (unsigned long long)(long long)sign;
+                chk += sign > 0 ? h : 0ull - h;
                 if (tuples) {
                     unsigned long long slot = atomicAdd(acc.tup, 1ull);
                     if (slot < cap) {
@@ -96,6 +104,7 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, int64_t e_lo, 
             uint64_t s = b0 + __popc(mask & lt);
             out.x[0][s] = x0;
             out.x[1][s] = x1;
+            if (out.sg) out.sg[s] = (int8_t)sign;
         }
     }
     if (emit) {
@@ -104,31 +113,37 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, int64_t e_lo, 
     }
 }
 
-// Count: min-c and min-i of every prefix of a level (ties: first binding atom).
-__global__ void __launch_bounds__(PT) k_count(Plan P, GraphView G, uint32_t j, Cols in, uint64_t n,
+// Count: min-c and min-i of every prefix of a level (ties: first binding
+// atom). cnt is the size of the chosen list's enumeration space (for a new
+// view that includes the batch's deletions, which Propose skips).
+__global__ void __launch_bounds__(PT) k_count(Plan P, GraphView G, DeltaView D, uint32_t j, Cols in, uint64_t n,
                                               uint32_t* __restrict__ cnt, uint8_t* __restrict__ mini) {
+    const DeltaView* Dv = P.delta ? &D : nullptr;
     const uint64_t stride = (uint64_t)gridDim.x * PT;
     for (uint64_t i = (uint64_t)blockIdx.x * PT + threadIdx.x; i < n; i += stride) {
-        int64_t best = INT64_MAX;
-        uint32_t bi = 0;
+        uint32_t best = 0xffffffffu, space = 0, bi = 0;
         for (uint32_t b = 0; b < P.nb[j]; b++) {
-            uint32_t v = in.x[P.bpos[j][b]][i];
-            const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
-            int64_t len = __ldg(off + v + 1) - __ldg(off + v);
-            if (len < best) { best = len; bi = b; }
+            const uint32_t v = in.x[P.bpos[j][b]][i];
+            const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], v);
+            if (L.degree() < best) {
+                best = L.degree();
+                space = L.space();
+                bi = b;
+            }
         }
-        cnt[i] = (uint32_t)best;
+        cnt[i] = space;
         mini[i] = (uint8_t)bi;
     }
 }
 
 // Propose + Intersect over candidates [c_lo, c_hi) of level j.
-__global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, uint32_t j, Cols in, uint64_t n,
+__global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, DeltaView D, uint32_t j, Cols in, uint64_t n,
                                                const int64_t* __restrict__ coff, const uint8_t* __restrict__ mini,
                                                int64_t c_lo, int64_t c_hi, int last, Cols out, Acc acc,
                                                uint32_t* __restrict__ tuples, uint64_t cap) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = gj_lanemask_lt();
+    const DeltaView* Dv = P.delta ? &D : nullptr;
     unsigned long long cnt = 0, chk = 0;
     const int64_t stride = (int64_t)gridDim.x * PT;
     for (int64_t base = c_lo + (int64_t)blockIdx.x * PT + (threadIdx.x & ~31); base < c_hi; base += stride) {
@@ -136,6 +151,7 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, uint32_t j, 
         bool keep = t < c_hi;
         uint32_t xs[GJ_MAX_K];
         uint64_t i = 0;
+        int sign = 1;
         if (keep) {
             // the prefix whose candidate range holds t: last i with coff[i] <= t
             uint64_t lo = 0, hi = n;
@@ -144,25 +160,24 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, uint32_t j, 
                 if (__ldg(coff + mid) <= t) lo = mid; else hi = mid;
             }
             i = lo;
-            int64_t r = t - __ldg(coff + i);
-            uint32_t b = mini[i];
+            const uint32_t r = (uint32_t)(t - __ldg(coff + i));
+            const uint32_t b = mini[i];
             for (uint32_t p = 0; p < j; p++) xs[p] = in.x[p][i];
-            const uint32_t* a;
-            int64_t len;
-            list_of(G, P.bdir[j][b], xs[P.bpos[j][b]], a, len);
-            uint32_t e = __ldg(a + r);
+            if (in.sg) sign = in.sg[i];
+            const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], xs[P.bpos[j][b]]);
+            const uint32_t e = r < L.base_len ? __ldg(L.base + r) : __ldg(L.ins + (r - L.base_len));
+            if (r < L.base_len && L.ndel) keep = !gj_contains(L.del, L.ndel, e);  // deleted in the new version
             xs[j] = e;
             for (uint32_t bb = 0; bb < P.nb[j] && keep; bb++) {
                 if (bb == b) continue;
-                const uint32_t v = xs[P.bpos[j][bb]];
-                keep = P.bdir[j][bb] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
-                                     : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
+                keep = gj_view_member(G, Dv, P.bdir[j][bb], P.bview[j][bb], xs[P.bpos[j][bb]], e);
             }
         }
         if (last) {
             if (keep) {
-                cnt += 1;
-                chk += hash_positions(P, xs);
+                const uint64_t h = hash_positions(P, xs);
+                cnt += (unsigned long long)(long long)sign;
+                chk += sign > 0 ? h : 0ull - h;
                 if (tuples) {
                     unsigned long long slot = atomicAdd(acc.tup, 1ull);
                     if (slot < cap)
@@ -180,6 +195,7 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, uint32_t j, 
         if (keep) {
             uint64_t s = b0 + __popc(mask & lt);
             for (uint32_t p = 0; p <= j; p++) out.x[p][s] = xs[p];
+            if (out.sg) out.sg[s] = (int8_t)sign;
         }
     }
     if (last) {
@@ -200,28 +216,34 @@ struct Level {
 
 }  // namespace
 
-int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t v_lo, uint32_t v_hi,
-                    int64_t* count, uint64_t* checksum, uint32_t* out_tuples, uint64_t cap, uint64_t* written) {
-    const Plan& P = q->plan;
+int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t v_lo, uint32_t v_hi,
+                         const DeltaBatch* delta, int64_t* count, uint64_t* checksum, uint32_t* out_tuples,
+                         uint64_t cap, uint64_t* written) {
     const uint32_t k = P.k;
     cudaStream_t st = ctx->stream;
     GraphView G = g->view();
+    DeltaView D = delta ? delta->view : DeltaView{};
+    DeltaBatch B = delta ? *delta : DeltaBatch{};
     gj_work_stats& W = ctx->work;
     memset(&W, 0, sizeof(W));
 
-    if (v_hi > g->n) v_hi = g->n;
-    if (v_lo > v_hi) v_lo = v_hi;
-    // seed edge range: the index slots keyed by x0 in [v_lo, v_hi)
-    const int64_t* soff = P.seed_dir ? g->rev.off : g->fwd.off;
     int64_t se[2] = {0, 0};
-    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&se[0], soff + v_lo, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&se[1], soff + v_hi, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (P.delta) {
+        se[1] = (int64_t)B.n;
+    } else {
+        if (v_hi > g->n) v_hi = g->n;
+        if (v_lo > v_hi) v_lo = v_hi;
+        // seed edge range: the index slots keyed by x0 in [v_lo, v_hi)
+        const int64_t* soff = P.seed_dir ? g->rev.off : g->fwd.off;
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&se[0], soff + v_lo, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&se[1], soff + v_hi, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    }
 
     // prefix buffers for levels 2..k-1, all with the same capacity
     uint64_t budget = ctx->opt.prefix_buffer_bytes ? ctx->opt.prefix_buffer_bytes : (512ull << 20);
     uint64_t per_slot = 0;
-    for (uint32_t j = 2; j < k; j++) per_slot += 4ull * j + 4 + 1 + 8;
+    for (uint32_t j = 2; j < k; j++) per_slot += 4ull * j + 4 + 1 + 8 + (P.delta ? 1 : 0);
     uint64_t capacity = per_slot ? budget / per_slot : 0;
     if (k > 2 && capacity < 1024) {
         gj_set_error(ctx, GJ_E_INVALID, "prefix_buffer_bytes too small");
@@ -239,6 +261,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
         };
         for (uint32_t j = 2; j < k; j++) {
             for (uint32_t p = 0; p < j; p++) L[j].cols.x[p] = (uint32_t*)take(4 * capacity);
+            L[j].cols.sg = P.delta ? (int8_t*)take(capacity) : nullptr;
             L[j].cnt = (uint32_t*)take(4 * capacity);
             L[j].mini = (uint8_t*)take(capacity);
             L[j].coff = (int64_t*)take(8 * (capacity + 1));
@@ -265,7 +288,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
         l.cursor = 0;
         l.total = 0;
         if (l.n == 0) return GJ_OK;
-        k_count<<<gj_div_up(l.n, PT) < grid ? gj_div_up(l.n, PT) : grid, PT, 0, st>>>(P, G, j, l.cols, l.n, l.cnt,
+        k_count<<<gj_div_up(l.n, PT) < grid ? gj_div_up(l.n, PT) : grid, PT, 0, st>>>(P, G, D, j, l.cols, l.n, l.cnt,
                                                                                        l.mini);
         GJ_LAUNCHED(ctx);
         GJ_TRY(gj_scan_u32(ctx, l.cnt, l.coff, l.n));
@@ -281,7 +304,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
     if (k == 2) {
         if (se[1] > se[0]) {
             gj_timer_begin(ctx);
-            k_seed<<<grid, PT, 0, st>>>(P, G, se[0], se[1], Cols{}, A, 1, tuples, cap);
+            k_seed<<<grid, PT, 0, st>>>(P, G, D, B, se[0], se[1], Cols{}, A, 1, tuples, cap);
             GJ_LAUNCHED(ctx);
             gj_timer_end(ctx);
         }
@@ -296,7 +319,8 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
                 int64_t chunk = se[1] - seed_cursor;
                 if ((uint64_t)chunk > capacity) chunk = (int64_t)capacity;
                 GJ_CUDA_TRY(ctx, cudaMemsetAsync(A.n_out, 0, 8, st));
-                k_seed<<<grid, PT, 0, st>>>(P, G, seed_cursor, seed_cursor + chunk, L[2].cols, A, 0, nullptr, 0);
+                k_seed<<<grid, PT, 0, st>>>(P, G, D, B, seed_cursor, seed_cursor + chunk, L[2].cols, A, 0, nullptr,
+                                            0);
                 GJ_LAUNCHED(ctx);
                 GJ_CUDA_TRY(ctx, cudaGetLastError());
                 seed_cursor += chunk;
@@ -308,8 +332,8 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
             Level& l = L[jd];
             if (jd == (int)k - 1) {
                 gj_timer_begin(ctx);
-                k_extend<<<grid, PT, 0, st>>>(P, G, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.total, 1, Cols{}, A,
-                                              tuples, cap);
+                k_extend<<<grid, PT, 0, st>>>(P, G, D, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.total, 1, Cols{},
+                                              A, tuples, cap);
                 GJ_LAUNCHED(ctx);
                 gj_timer_end(ctx);
                 GJ_CUDA_TRY(ctx, cudaGetLastError());
@@ -319,7 +343,7 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
             int64_t w = l.total - l.cursor;
             if ((uint64_t)w > window) w = (int64_t)window;
             GJ_CUDA_TRY(ctx, cudaMemsetAsync(A.n_out, 0, 8, st));
-            k_extend<<<grid, PT, 0, st>>>(P, G, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.cursor + w, 0,
+            k_extend<<<grid, PT, 0, st>>>(P, G, D, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.cursor + w, 0,
                                           L[jd + 1].cols, A, nullptr, 0);
             GJ_LAUNCHED(ctx);
             GJ_CUDA_TRY(ctx, cudaGetLastError());
@@ -344,4 +368,9 @@ int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t 
         *written = 0;
     }
     return GJ_OK;
+}
+
+int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t v_lo, uint32_t v_hi,
+                    int64_t* count, uint64_t* checksum, uint32_t* out_tuples, uint64_t cap, uint64_t* written) {
+    return gj_engine_plain_plan(ctx, g, q->plan, v_lo, v_hi, nullptr, count, checksum, out_tuples, cap, written);
 }

@@ -77,6 +77,7 @@ struct gj_graph {
     uint32_t n = 0;
     uint64_t m = 0;
     uint64_t version = 0;
+    uint64_t last_changes = 0;  // normalised changes of the last applied batch
     gj_csr fwd;  // out-neighbours
     gj_csr rev;  // in-neighbours
     GraphView view() const {
@@ -109,6 +110,38 @@ struct Plan {
     uint8_t bpos[GJ_MAX_K][GJ_MAX_ATOMS];
     uint8_t bdir[GJ_MAX_K][GJ_MAX_ATOMS];
     uint8_t batom[GJ_MAX_K][GJ_MAX_ATOMS];
+    // Delta queries (Section 3.3.1): which version each atom reads, 0 = the
+    // committed graph (old), 1 = the committed graph plus the batch (new).
+    // Static plans leave these 0.
+    uint8_t bview[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t sf_view[GJ_MAX_ATOMS];
+    uint32_t delta;  // 1: seeds are the batch's signed changes of atom seed_atom
+};
+
+enum { GJ_VIEW_OLD = 0, GJ_VIEW_NEW = 1 };
+
+// The normalised changes of one batch, on the device. chg_* are sorted by
+// (src, dst); per index direction, ins/del hold the inserted / deleted
+// entries sorted by (list owner, neighbour).
+struct DeltaSide {
+    const uint32_t* ins_key;
+    const uint32_t* ins_nbr;
+    uint32_t nins;
+    const uint32_t* del_key;
+    const uint32_t* del_nbr;
+    uint32_t ndel;
+};
+
+struct DeltaView {
+    DeltaSide fwd, rev;
+};
+
+struct DeltaBatch {
+    const uint32_t* chg_src = nullptr;
+    const uint32_t* chg_dst = nullptr;
+    const int8_t* chg_sign = nullptr;
+    uint64_t n = 0;
+    DeltaView view{};
 };
 
 struct gj_query {
@@ -117,10 +150,14 @@ struct gj_query {
     uint32_t as[GJ_MAX_ATOMS], ad[GJ_MAX_ATOMS];
     uint32_t order[GJ_MAX_K];
     Plan plan;
+    Plan dplan[GJ_MAX_ATOMS];  // delta queries dQ_i, one per atom
 };
 
 int gj_plan_compile(const uint32_t* as, const uint32_t* ad, uint32_t natoms, uint32_t k, const uint32_t* order,
                     Plan* out, std::string* why);
+// Plan of delta query dQ_i of q (Section 3.3.1): seeded from the changes of
+// atom i, atoms before i read the new version, atoms after i the old one.
+int gj_plan_compile_delta(const gj_query* q, uint32_t i, Plan* out, std::string* why);
 
 // ------------------------------------------------------------------ context
 
@@ -174,12 +211,34 @@ int gj_scan_i64(gj_ctx* ctx, const int64_t* in, int64_t* out, uint64_t n);
 // Sorts n 64-bit keys whose significant bits are [0, bits). keys and tmp
 // are n long; the sorted keys end in *result (keys or tmp).
 int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, uint64_t** result);
+// Stable key-value variant: vals move with their keys (equal keys keep input order).
+int gj_radix_sort_kv(gj_ctx* ctx, uint64_t* keys, uint64_t* ktmp, uint32_t* vals, uint32_t* vtmp, uint64_t n, int bits,
+                     uint64_t** kresult, uint32_t** vresult);
 
 int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m, uint32_t n, gj_graph* g);
 
 // Engines: count (and checksum) of a query over the matches whose x0 lies in [v_lo, v_hi).
 int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t v_lo, uint32_t v_hi,
                     int64_t* count, uint64_t* checksum, uint32_t* out_tuples, uint64_t cap, uint64_t* written);
+// The same for an explicit plan; with delta non-null the seeds are the
+// batch's changes and every match counts with its seed's sign.
+int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t v_lo, uint32_t v_hi,
+                         const DeltaBatch* delta, int64_t* count, uint64_t* checksum, uint32_t* out_tuples,
+                         uint64_t cap, uint64_t* written);
+
+// Device buffers of one normalised batch (owned; released by gj_delta_free).
+struct DeltaBuf {
+    void* mem = nullptr;
+    DeltaBatch batch;
+};
+// Normalises an update batch against g (R' = R + Delta R, Section 3.3.1):
+// per edge the last update decides, self-loops are dropped, only edges
+// whose presence changes remain. Inputs may be host or device arrays.
+int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign,
+                     uint64_t b, DeltaBuf* out);
+void gj_delta_free(gj_ctx* ctx, DeltaBuf* d);
+// Replaces g's indices by those of g + delta (the commit).
+int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d);
 
 // One launch over nq queries; counts/checksums are host arrays of nq.
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
@@ -248,6 +307,71 @@ __device__ __forceinline__ bool gj_list_member(const int64_t* __restrict__ off, 
     const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s);
     if (len >= GJ_HASH_MIN_DEG) return gj_tab_member(tab + __ldg(tab_off + v), gj_tab_bits(len), e);
     return gj_contains(nbr + s, len, e);
+}
+
+// [lo, hi) of the entries owned by v in a key-sorted array.
+__device__ __forceinline__ void gj_key_range(const uint32_t* __restrict__ key, uint32_t n, uint32_t v, uint32_t& lo,
+                                             uint32_t& hi) {
+    uint32_t a = 0, b = n;
+    while (a < b) {
+        uint32_t mid = (a + b) >> 1;
+        if (__ldg(key + mid) < v) a = mid + 1; else b = mid;
+    }
+    lo = a;
+    b = n;
+    while (a < b) {
+        uint32_t mid = (a + b) >> 1;
+        if (__ldg(key + mid) <= v) a = mid + 1; else b = mid;
+    }
+    hi = a;
+}
+
+// A list of vertex v as seen by one view: the committed list, plus (new
+// view only) the batch's inserted entries and the deleted ones to skip.
+// Enumeration space: [0, base_len) committed entries, then the inserts.
+struct ViewList {
+    const uint32_t* base;
+    uint32_t base_len;
+    const uint32_t* ins;
+    uint32_t nins;
+    const uint32_t* del;
+    uint32_t ndel;
+    __device__ uint32_t degree() const { return base_len + nins - ndel; }
+    __device__ uint32_t space() const { return base_len + nins; }
+};
+
+__device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
+                                                 uint32_t v) {
+    const int64_t* off = dir ? G.ro : G.fo;
+    const int64_t s = __ldg(off + v);
+    ViewList L{(dir ? G.rn : G.fn) + s, (uint32_t)(__ldg(off + v + 1) - s), nullptr, 0, nullptr, 0};
+    if (view == GJ_VIEW_NEW && D) {
+        const DeltaSide& S = dir ? D->rev : D->fwd;
+        uint32_t lo, hi;
+        gj_key_range(S.ins_key, S.nins, v, lo, hi);
+        L.ins = S.ins_nbr + lo;
+        L.nins = hi - lo;
+        gj_key_range(S.del_key, S.ndel, v, lo, hi);
+        L.del = S.del_nbr + lo;
+        L.ndel = hi - lo;
+    }
+    return L;
+}
+
+// Membership of x in v's list under a view: the batch's changes of v
+// first (they are normalised: inserts are absent from the committed list,
+// deletes present), then the committed index.
+__device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
+                                               uint32_t v, uint32_t x) {
+    if (view == GJ_VIEW_NEW && D) {
+        const DeltaSide& S = dir ? D->rev : D->fwd;
+        uint32_t lo, hi;
+        gj_key_range(S.ins_key, S.nins, v, lo, hi);
+        if (gj_contains(S.ins_nbr + lo, hi - lo, x)) return true;
+        gj_key_range(S.del_key, S.ndel, v, lo, hi);
+        if (gj_contains(S.del_nbr + lo, hi - lo, x)) return false;
+    }
+    return dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
 }
 
 __device__ __forceinline__ uint32_t gj_lanemask_lt() {

@@ -71,3 +71,79 @@ int gj_plan_compile(const uint32_t* as, const uint32_t* ad, uint32_t natoms, uin
     }
     return GJ_OK;
 }
+
+// Delta query dQ_i (Section 3.3.1): the attribute order starts with atom
+// i's attributes (source, destination) and continues with, repeatedly, the
+// first attribute in q's order that shares an atom with a bound one (the
+// paper allows any order after R_i's attributes; this keeps every later
+// level bound by at least one atom). Atoms before i in definition order read
+// the new version, atoms after i the old one (Section 4.3); atom i itself
+// is the seed, so its changes enter once, with their signs.
+int gj_plan_compile_delta(const gj_query* q, uint32_t i, Plan* p, std::string* why) {
+    auto bad = [&](const char* m) {
+        if (why) *why = m;
+        return GJ_E_INVALID;
+    };
+    const uint32_t k = q->k, natoms = q->natoms;
+    if (i >= natoms) return bad("atom index out of range");
+    memset(p, 0, sizeof(*p));
+    p->k = k;
+    p->natoms = natoms;
+    p->delta = 1;
+    uint32_t n = 0, bound = 0;
+    auto bind = [&](uint32_t a) {
+        p->order[n] = a;
+        p->qpos[a] = n;
+        n++;
+        bound |= 1u << a;
+    };
+    bind(q->as[i]);
+    bind(q->ad[i]);
+    while (n < k) {
+        bool found = false;
+        for (uint32_t jj = 0; jj < k && !found; jj++) {
+            uint32_t a = q->order[jj];
+            if (bound & (1u << a)) continue;
+            for (uint32_t t = 0; t < natoms; t++) {
+                if ((q->as[t] == a && (bound & (1u << q->ad[t]))) || (q->ad[t] == a && (bound & (1u << q->as[t])))) {
+                    found = true;
+                    break;
+                }
+            }
+            if (found) bind(a);
+        }
+        if (!found) return bad("the query graph is not connected");
+    }
+    p->seed_atom = i;
+    p->seed_dir = 0;
+    for (uint32_t t = 0; t < natoms; t++) {
+        if (t == i) continue;
+        uint32_t ps = p->qpos[q->as[t]], pd = p->qpos[q->ad[t]];
+        if (ps <= 1 && pd <= 1) {
+            p->sf_dir[p->nsf] = (uint8_t)(ps == 0 ? 0 : 1);
+            p->sf_atom[p->nsf] = (uint8_t)t;
+            p->sf_view[p->nsf] = (uint8_t)(t < i ? GJ_VIEW_NEW : GJ_VIEW_OLD);
+            p->nsf++;
+        }
+    }
+    for (uint32_t j = 2; j < k; j++) {
+        uint32_t nb = 0;
+        for (uint32_t t = 0; t < natoms; t++) {
+            if (t == i) continue;
+            uint32_t ps = p->qpos[q->as[t]], pd = p->qpos[q->ad[t]];
+            int dir = -1;
+            uint32_t bp = 0;
+            if (pd == j && ps < j) { dir = 0; bp = ps; }
+            else if (ps == j && pd < j) { dir = 1; bp = pd; }
+            if (dir < 0) continue;
+            p->bpos[j][nb] = (uint8_t)bp;
+            p->bdir[j][nb] = (uint8_t)dir;
+            p->batom[j][nb] = (uint8_t)t;
+            p->bview[j][nb] = (uint8_t)(t < i ? GJ_VIEW_NEW : GJ_VIEW_OLD);
+            nb++;
+        }
+        if (nb == 0) return bad("an attribute shares no atom with any earlier attribute of the order");
+        p->nb[j] = nb;
+    }
+    return GJ_OK;
+}

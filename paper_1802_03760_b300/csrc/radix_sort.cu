@@ -29,9 +29,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t* __restri
     hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+template <bool VALUES>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __restrict__ keys, uint64_t n, int shift,
                                                           const int64_t* __restrict__ digit_off, uint32_t ntiles,
-                                                          uint64_t* __restrict__ out) {
+                                                          uint64_t* __restrict__ out, const uint32_t* __restrict__ vin,
+                                                          uint32_t* __restrict__ vout) {
     __shared__ uint32_t wcount[RS_WARPS][RS_BINS];
     __shared__ int64_t boff[RS_BINS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -41,12 +43,14 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
     const uint64_t wbase = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)warp * 32 * RS_ITEMS;
     uint64_t k[RS_ITEMS];
     uint32_t rank[RS_ITEMS];
+    uint32_t val[VALUES ? RS_ITEMS : 1];
     const uint32_t lt = gj_lanemask_lt();
 #pragma unroll
     for (int j = 0; j < RS_ITEMS; j++) {
         uint64_t i = wbase + (uint64_t)j * 32 + lane;
         bool valid = i < n;
         k[j] = valid ? keys[i] : 0;
+        if (VALUES) val[j] = valid ? vin[i] : 0;
         uint32_t d = valid ? ((uint32_t)(k[j] >> shift) & 0xffu) : RS_BINS;  // invalid lanes form their own group
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = (d < RS_BINS) ? wcount[warp][d] : 0;
@@ -74,15 +78,21 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t* __res
         uint64_t i = wbase + (uint64_t)j * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)(k[j] >> shift) & 0xffu;
-            out[boff[d] + wcount[warp][d] + rank[j]] = k[j];
+            const int64_t pos = boff[d] + wcount[warp][d] + rank[j];
+            out[pos] = k[j];
+            if (VALUES) vout[pos] = val[j];
         }
     }
 }
 
 }  // namespace
 
-int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, uint64_t** result) {
+namespace {
+
+int radix_sort_impl(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint32_t* vals, uint32_t* vtmp, uint64_t n, int bits,
+                    uint64_t** result, uint32_t** vresult) {
     *result = keys;
+    if (vresult) *vresult = vals;
     if (n <= 1 || bits <= 0) return GJ_OK;
     uint32_t ntiles = gj_div_up(n, RS_TILE);
     uint64_t nh = (uint64_t)RS_BINS * ntiles;
@@ -91,17 +101,38 @@ int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, in
     int64_t* off = (int64_t*)(((uintptr_t)(hist + nh) + 255) & ~(uintptr_t)255);
     uint64_t* src = keys;
     uint64_t* dst = tmp;
+    uint32_t* vsrc = vals;
+    uint32_t* vdst = vtmp;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, hist, ntiles);
         GJ_LAUNCHED(ctx);
         GJ_TRY(gj_scan_u32(ctx, hist, off, nh));
-        k_rs_scatter<<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, off, ntiles, dst);
+        if (vals)
+            k_rs_scatter<true><<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, off, ntiles, dst, vsrc, vdst);
+        else
+            k_rs_scatter<false><<<ntiles, RS_THREADS, 0, ctx->stream>>>(src, n, shift, off, ntiles, dst, nullptr,
+                                                                        nullptr);
         GJ_LAUNCHED(ctx);
         GJ_CUDA_TRY(ctx, cudaGetLastError());
         uint64_t* t = src;
         src = dst;
         dst = t;
+        uint32_t* vt = vsrc;
+        vsrc = vdst;
+        vdst = vt;
     }
     *result = src;
+    if (vresult) *vresult = vsrc;
     return GJ_OK;
+}
+
+}  // namespace
+
+int gj_radix_sort_u64(gj_ctx* ctx, uint64_t* keys, uint64_t* tmp, uint64_t n, int bits, uint64_t** result) {
+    return radix_sort_impl(ctx, keys, tmp, nullptr, nullptr, n, bits, result, nullptr);
+}
+
+int gj_radix_sort_kv(gj_ctx* ctx, uint64_t* keys, uint64_t* ktmp, uint32_t* vals, uint32_t* vtmp, uint64_t n, int bits,
+                     uint64_t** kresult, uint32_t** vresult) {
+    return radix_sort_impl(ctx, keys, ktmp, vals, vtmp, n, bits, kresult, vresult);
 }

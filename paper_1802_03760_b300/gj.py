@@ -72,6 +72,9 @@ _SIGS = {
     "gj_count_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, _I64P, _U64P]),
     "gj_last_work": (ctypes.c_int, [_VP, ctypes.POINTER(WorkStats)]),
     "gj_list": (ctypes.c_int, [_VP, _VP, _U32P, ctypes.c_uint64, _U64P, _I64P, _U64P]),
+    "gj_apply_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.POINTER(_VP), ctypes.c_uint32,
+                                      _I64P, _U64P]),
+    "gj_graph_last_batch": (ctypes.c_int, [_VP, _U64P]),
     "gj_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "gj_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _U64P]),
     "gj_ctx_stream": (_VP, [_VP]),
@@ -271,6 +274,36 @@ def count_noalloc(g: Graph, qs):
     h = np.zeros(max(n, 1), np.uint64)
     _check(lib().gj_count_noalloc(g._h, arr, n, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
     return [int(x) for x in c[:n]], [int(x) for x in h[:n]]
+
+
+def _ptr8(a):
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        return ctypes.c_void_p(a.data_ptr()), a
+    arr = np.ascontiguousarray(a, dtype=np.int8)
+    return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def apply_batch(g: Graph, src, dst, sign, qs=()):
+    """Applies one update batch; returns ([delta counts], [delta checksums]) of qs."""
+    ps, ks = _ptr(src)
+    pd, kd = _ptr(dst)
+    pg, kg = _ptr8(sign)
+    b = len(src)
+    n = len(qs)
+    arr = (_VP * max(n, 1))(*[q._h for q in qs])
+    c = np.zeros(max(n, 1), np.int64)
+    h = np.zeros(max(n, 1), np.uint64)
+    _check(lib().gj_apply_batch(g._h, ps, pd, pg, b, arr if n else None, n, c.ctypes.data_as(_I64P) if n else None,
+                                h.ctypes.data_as(_U64P) if n else None), g.ctx)
+    return [int(x) for x in c[:n]], [int(x) for x in h[:n]]
+
+
+def last_batch_changes(g: Graph) -> int:
+    c = ctypes.c_uint64(0)
+    _check(lib().gj_graph_last_batch(g._h, ctypes.byref(c)), g.ctx)
+    return c.value
 
 
 def list_matches(g: Graph, q: Query, cap: int):
