@@ -221,6 +221,47 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
 /* Number of edges whose presence the last gj_apply_batch on g changed. */
 int gj_graph_last_batch(const gj_graph* g, uint64_t* changes);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * A request loop on one graph: count requests and update batches are
+ * submitted from any thread and run in submission order, each seeing the
+ * graph versions it would see if the requests ran one by one. Count
+ * requests that are queued together run as one fused launch (continuous
+ * batching); an update batch overlaps with count launches already running,
+ * which keep reading the previous version of the index. Requests are
+ * admitted against a device-memory budget. While serving, use only
+ * gj_submit_count, gj_submit_batch, gj_poll and gj_serve_stop on the
+ * context; other calls on it return GJ_E_INVALID. Queries passed to a
+ * request must stay alive until the request is polled.
+ */
+typedef struct {
+    uint64_t req_id;
+    int32_t status;          /* GJ_OK, or the request's own error (e.g. GJ_E_ADMIT) */
+    uint32_t kind;           /* 0 = count request, 1 = update batch */
+    uint32_t nq;
+    uint32_t reserved;
+    int64_t counts[64];      /* count request: counts; batch: delta counts */
+    uint64_t checksums[64];  /* count request: checksums; batch: delta checksums */
+    uint64_t version;        /* count: the version it read; batch: the version it committed */
+    double submit_ms, start_ms, end_ms;  /* host times since gj_serve_start */
+} gj_result;
+
+/* Starts the request loop on g. memory_budget_bytes = 0: 80% of the free
+ * device memory. Errors: GJ_E_INVALID (already serving), GJ_E_CUDA. */
+int gj_serve_start(gj_ctx* ctx, gj_graph* g, uint64_t memory_budget_bytes);
+/* Finishes every submitted request, then stops the loop. */
+int gj_serve_stop(gj_ctx* ctx);
+/* Queues a count of nq <= 64 queries; *req_id identifies it for gj_poll. */
+int gj_submit_count(gj_ctx* ctx, const gj_query* const* qs, uint32_t nq, uint64_t* req_id);
+/* Queues an update batch (copied before return; host or device arrays) and
+ * the nq <= 64 queries whose deltas it reports (see gj_apply_batch). */
+int gj_submit_batch(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, const int8_t* sign, uint64_t b,
+                    const gj_query* const* qs, uint32_t nq, uint64_t* req_id);
+/* Waits up to wait_ms (-1: without limit, 0: not at all) for a request; on
+ * GJ_OK *out holds its result and the request is retired. GJ_E_PENDING if
+ * it is still running, GJ_E_NOTFOUND for an unknown or retired id. */
+int gj_poll(gj_ctx* ctx, uint64_t req_id, int wait_ms, gj_result* out);
+
 /* Kernel timing: when enabled, the launches of the dominant kernel of each
  * count call are bracketed by CUDA events on the context's stream and their
  * durations summed. gj_profile_read returns and clears the totals. */

@@ -154,6 +154,7 @@ int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
 
 void gj_destroy(gj_ctx* ctx) {
     if (!ctx) return;
+    if (ctx->server) gj_serve_stop(ctx);
     DevSet ds(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     for (auto& a : ctx->scratch)
@@ -194,6 +195,7 @@ int gj_profile_read(gj_ctx* ctx, double* total_ms, uint64_t* launches) {
 
 void gj_graph_free(gj_graph* g) {
     if (!g) return;
+    if (g->ctx->server) gj_serve_stop(g->ctx);  // the loop may still read g
     DevSet ds(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
     for (gj_csr* c : {&g->fwd, &g->rev}) {
@@ -302,6 +304,7 @@ int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, 
                 uint64_t* checksum, gj_work_stats* stats) {
     if (!g || !q || !count || !checksum || q->ctx != g->ctx || engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     int rc;
@@ -319,6 +322,7 @@ int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t 
     for (uint32_t i = 0; i < nq; i++)
         if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, 0, UINT32_MAX, counts, checksums);
@@ -356,6 +360,7 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
     for (uint32_t i = 0; i < nq; i++)
         if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeltaBuf buf;
@@ -405,6 +410,7 @@ int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, 
     if (!g || !q || !written || !total || !checksum || (cap && !out_tuples) || q->ctx != g->ctx)
         return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     int64_t c = 0;

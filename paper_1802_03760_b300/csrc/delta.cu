@@ -293,7 +293,13 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
     return GJ_OK;
 }
 
-int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d) {
+void gj_csr_release(gj_csr& c) {
+    for (void* p : {(void*)c.off, (void*)c.nbr, (void*)c.key, (void*)c.tab_off, (void*)c.tab})
+        if (p) cudaFree(p);
+    c = gj_csr{};
+}
+
+int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_fwd, gj_csr* old_rev) {
     cudaStream_t st = ctx->stream;
     if (d.n == 0) {
         g->version++;
@@ -326,19 +332,19 @@ int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d) {
     fresh.ctx = ctx;
     if (rc == GJ_OK) rc = gj_csr_build(ctx, nsrc, ndst, (uint64_t)kept + d.view.fwd.nins, g->n, &fresh);
     cudaFreeAsync(mem, st);
-    auto release = [](gj_csr& c) {
-        for (void* p : {(void*)c.off, (void*)c.nbr, (void*)c.key, (void*)c.tab_off, (void*)c.tab})
-            if (p) cudaFree(p);
-        c = gj_csr{};
-    };
     if (rc != GJ_OK) {
-        release(fresh.fwd);
-        release(fresh.rev);
+        gj_csr_release(fresh.fwd);
+        gj_csr_release(fresh.rev);
         return rc;
     }
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    release(g->fwd);
-    release(g->rev);
+    if (old_fwd && old_rev) {
+        *old_fwd = g->fwd;
+        *old_rev = g->rev;
+    } else {
+        gj_csr_release(g->fwd);
+        gj_csr_release(g->rev);
+    }
     g->fwd = fresh.fwd;
     g->rev = fresh.rev;
     g->m = fresh.m;

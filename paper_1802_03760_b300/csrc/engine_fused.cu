@@ -525,6 +525,47 @@ __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint3
 
 int gj_fused_smem_bytes(uint32_t kmax) { return (int)(warp_bytes(kmax) * FW); }
 
+size_t gj_fused_async_bytes(uint32_t nq) {
+    const size_t plan_bytes = ((sizeof(Plan) * nq) + 255) & ~(size_t)255;
+    return plan_bytes + 8 * (4 * (size_t)nq + 2) + 8 * (2 * (size_t)nq) + 8 * 64 + 1024;
+}
+
+// Enqueues one fused launch over nq plans on stream st, with all device
+// state in dscratch (gj_fused_async_bytes(nq) bytes); nothing waits. On
+// completion the counts and checksums are at *results: nq counts followed
+// by nq checksums.
+int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t nq, cudaStream_t st, void* dscratch,
+                     unsigned long long** results) {
+    const size_t plan_bytes = ((sizeof(Plan) * nq) + 255) & ~(size_t)255;
+    char* base = (char*)dscratch;
+    Plan* d_plans = (Plan*)base;
+    int64_t* seed_lo = (int64_t*)(base + plan_bytes);
+    int64_t* seed_n = seed_lo + nq;
+    uint64_t* qbase = (uint64_t*)(seed_n + nq);
+    unsigned long long* counts_d = (unsigned long long*)(qbase + nq + 1);
+    unsigned long long* chks_d = counts_d + nq;
+    unsigned long long* next = chks_d + nq;
+    unsigned long long* stats = next + 1;
+    uint32_t kmax = 2;
+    for (uint32_t q = 0; q < nq; q++) kmax = hp[q].k > kmax ? hp[q].k : kmax;
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp, sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase);
+    GJ_LAUNCHED(ctx);
+    const int smem = gj_fused_smem_bytes(kmax);
+    if (smem > 48 * 1024)
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    GJ_LAUNCHED(ctx);
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    *results = counts_d;
+    return GJ_OK;
+}
+
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums) {
     if (nq == 0) return GJ_OK;
@@ -701,6 +742,7 @@ extern "C" int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t
                                 uint64_t* checksums) {
     if (!g || !qs || !counts || !checksums || nq == 0) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
     if (nq > NOALLOC_MAX_QUERIES) {
         gj_set_error(ctx, GJ_E_INVALID, "gj_count_noalloc: at most 64 queries per call");
         return GJ_E_INVALID;

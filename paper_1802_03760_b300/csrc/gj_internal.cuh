@@ -188,6 +188,7 @@ struct gj_ctx {
     std::mutex mu;
     gj_work_stats work{};        // units processed by the last count call
     uint64_t launches = 0;       // kernels launched on this context (host-side count)
+    struct gj_server* server = nullptr;  // request loop, while serving
 };
 
 // Counts one kernel launch of ctx (gj_launch_count reports the total).
@@ -237,13 +238,20 @@ struct DeltaBuf {
 int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign,
                      uint64_t b, DeltaBuf* out);
 void gj_delta_free(gj_ctx* ctx, DeltaBuf* d);
-// Replaces g's indices by those of g + delta (the commit).
-int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d);
+// Replaces g's indices by those of g + delta (the commit). With old_fwd /
+// old_rev given, the previous index arrays are handed back instead of freed
+// (readers still in flight keep using them).
+int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_fwd = nullptr,
+                    gj_csr* old_rev = nullptr);
+void gj_csr_release(gj_csr& c);
 
 // One launch over nq queries; counts/checksums are host arrays of nq.
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums);
 int gj_fused_smem_bytes(uint32_t kmax);
+size_t gj_fused_async_bytes(uint32_t nq);
+int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t nq, cudaStream_t st, void* dscratch,
+                     unsigned long long** results);
 
 // ------------------------------------------------------------------ device helpers
 

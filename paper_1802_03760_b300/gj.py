@@ -47,6 +47,20 @@ class WorkStats(ctypes.Structure):
                 "proposals": list(self.proposals), "produced": list(self.produced)}
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_uint32),
+                ("nq", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("counts", ctypes.c_int64 * 64),
+                ("checksums", ctypes.c_uint64 * 64), ("version", ctypes.c_uint64), ("submit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.nq
+        return {"req_id": self.req_id, "status": self.status, "kind": "count" if self.kind == 0 else "batch",
+                "counts": [int(x) for x in self.counts[:n]], "checksums": [int(x) for x in self.checksums[:n]],
+                "version": self.version, "submit_ms": self.submit_ms, "start_ms": self.start_ms,
+                "end_ms": self.end_ms, "latency_ms": self.end_ms - self.submit_ms}
+
+
 _lib = None
 
 _VP = ctypes.c_void_p
@@ -75,6 +89,12 @@ _SIGS = {
     "gj_apply_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.POINTER(_VP), ctypes.c_uint32,
                                       _I64P, _U64P]),
     "gj_graph_last_batch": (ctypes.c_int, [_VP, _U64P]),
+    "gj_serve_start": (ctypes.c_int, [_VP, _VP, ctypes.c_uint64]),
+    "gj_serve_stop": (ctypes.c_int, [_VP]),
+    "gj_submit_count": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, _U64P]),
+    "gj_submit_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.POINTER(_VP), ctypes.c_uint32,
+                                       _U64P]),
+    "gj_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(Result)]),
     "gj_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
     "gj_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _U64P]),
     "gj_ctx_stream": (_VP, [_VP]),
@@ -304,6 +324,51 @@ def last_batch_changes(g: Graph) -> int:
     c = ctypes.c_uint64(0)
     _check(lib().gj_graph_last_batch(g._h, ctypes.byref(c)), g.ctx)
     return c.value
+
+
+class Server:
+    """The request loop of a context on one graph (gj_serve_start .. gj_serve_stop)."""
+
+    def __init__(self, g: Graph, memory_budget_bytes: int = 0):
+        self.g = g
+        self.ctx = g.ctx
+        self._keep = {}
+        _check(lib().gj_serve_start(self.ctx._h, g._h, memory_budget_bytes), self.ctx)
+        self.running = True
+
+    def submit_count(self, qs) -> int:
+        arr = (_VP * len(qs))(*[q._h for q in qs])
+        rid = ctypes.c_uint64(0)
+        _check(lib().gj_submit_count(self.ctx._h, arr, len(qs), ctypes.byref(rid)), self.ctx)
+        self._keep[rid.value] = list(qs)
+        return rid.value
+
+    def submit_batch(self, src, dst, sign, qs=()) -> int:
+        ps, ks = _ptr(src)
+        pd, kd = _ptr(dst)
+        pg, kg = _ptr8(sign)
+        n = len(qs)
+        arr = (_VP * max(n, 1))(*[q._h for q in qs])
+        rid = ctypes.c_uint64(0)
+        _check(lib().gj_submit_batch(self.ctx._h, ps, pd, pg, len(src), arr if n else None, n, ctypes.byref(rid)),
+               self.ctx)
+        self._keep[rid.value] = list(qs)
+        return rid.value
+
+    def poll(self, rid: int, wait_ms: int = -1):
+        """The request's result as a dict, or None while it is pending."""
+        r = Result()
+        rc = lib().gj_poll(self.ctx._h, rid, wait_ms, ctypes.byref(r))
+        if rc == -9:
+            return None
+        _check(rc, self.ctx)
+        self._keep.pop(rid, None)
+        return r.as_dict()
+
+    def stop(self):
+        if self.running:
+            _check(lib().gj_serve_stop(self.ctx._h), self.ctx)
+            self.running = False
 
 
 def list_matches(g: Graph, q: Query, cap: int):
