@@ -411,6 +411,130 @@ def run_delta(args):
     return 0
 
 
+def serve_trace(scale, hubs, hub_deg, nreq, seed=1):
+    """Base graph (R-MAT plus planted hubs) and a seeded request mix: half
+    counts of one query (triangle, diamond or 4-clique), half update batches
+    of log-uniform size in [1e3, 1e5] reporting delta triangle and 4-clique."""
+    from paper_1802_03760_b300.inputs import UpdateStream, hub_edges
+    s, d = rmat_edges(scale, seed=seed)
+    _, hs, hd = hub_edges(1 << scale, hubs, hub_deg, seed=seed)
+    s = np.concatenate([s, hs])
+    d = np.concatenate([d, hd])
+    stream = UpdateStream(s, d, scale, seed=seed)
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for _ in range(nreq):
+        if rng.random() < 0.5:
+            reqs.append(("count", None, [BENCH_QUERIES[int(rng.integers(0, 3))]]))
+        else:
+            b = int(round(10 ** rng.uniform(3, 5)))
+            reqs.append(("batch", stream.next_batch(b), ["triangle", "4-clique"]))
+    return s, d, reqs
+
+
+def run_serve(args):
+    """Requests arrive as a Poisson process at f x the capacity of the
+    sequential plain path (f = 0.5, 0.8, 0.95). Served: submitted to the
+    request loop at their arrival times. Plain: the same trace handled one
+    request at a time, in order, through the synchronous API with the
+    level-synchronous engine. Latency = completion - arrival."""
+    import threading
+    import torch
+    from paper_1802_03760_b300 import gj
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    scale = args.scale if args.scale != SCALE else 16
+    n = 1 << scale
+    s, d, reqs = serve_trace(scale, 32, args.hub_degree, args.requests)
+    rng = np.random.default_rng(2)
+
+    def fresh():
+        ctx = gj.Context(local, engine=gj.ENGINE_PLAIN)
+        g = gj.Graph(ctx, s, d, n)
+        qmap = {nm: gj.Query(ctx, *QUERIES[nm]) for nm in BENCH_QUERIES}
+        return ctx, g, qmap
+
+    def run_plain(arrivals):
+        ctx, g, qmap = fresh()
+        t0 = time.perf_counter()
+        lat, res = [], []
+        for (kind, batch, names), a in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            qs = [qmap[nm] for nm in names]
+            if kind == "count":
+                r = gj.count_many(g, qs, engine=gj.ENGINE_PLAIN)
+            else:
+                r = gj.apply_batch(g, *batch, qs)
+            res.append(r)
+            lat.append((time.perf_counter() - t0 - a) * 1e3)
+        span = time.perf_counter() - t0
+        ctx.close()
+        return lat, res, span
+
+    def run_served(arrivals):
+        ctx, g, qmap = fresh()
+        srv = gj.Server(g)
+        ids = [None] * len(reqs)
+        sub_t = [0.0] * len(reqs)
+        t0 = time.perf_counter()
+
+        def submitter():
+            for i, ((kind, batch, names), a) in enumerate(zip(reqs, arrivals)):
+                now = time.perf_counter() - t0
+                if now < a:
+                    time.sleep(a - now)
+                qs = [qmap[nm] for nm in names]
+                ids[i] = srv.submit_count(qs) if kind == "count" else srv.submit_batch(*batch, qs)
+                sub_t[i] = time.perf_counter() - t0
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        out = [srv.poll(i) for i in ids]
+        srv.stop()
+        ctx.close()
+        # the loop's own clock gives each request's time in the system; add the
+        # submitter's lag behind the arrival time
+        lat = [(o["end_ms"] - o["submit_ms"]) + (st - a) * 1e3 for o, st, a in zip(out, sub_t, arrivals)]
+        span = max(a + l / 1e3 for a, l in zip(arrivals, lat))
+        res = [(o["counts"], o["checksums"]) for o in out]
+        return lat, res, span
+
+    # capacity of the plain path: back-to-back service of the trace
+    lat0, ref, span0 = run_plain([0.0] * len(reqs))
+    capacity = len(reqs) / span0
+    loads = {}
+    for f in (0.5, 0.8, 0.95):
+        gaps = rng.exponential(1.0 / (f * capacity), len(reqs))
+        arrivals = list(np.cumsum(gaps) - gaps[0])
+        lp, rp, sp = run_plain(arrivals)
+        ls, rs, ss = run_served(arrivals)
+        if [tuple(map(tuple, r)) for r in rp] != [tuple(map(tuple, r)) for r in rs] or \
+                [tuple(map(tuple, r)) for r in rp] != [tuple(map(tuple, r)) for r in ref]:
+            raise RuntimeError("served results differ from the sequential plain path")
+        loads[str(f)] = {"arrival_rate_per_s": f * capacity,
+                         "served": {"p50_ms": float(np.percentile(ls, 50)), "p99_ms": float(np.percentile(ls, 99)),
+                                    "throughput_req_per_s": len(reqs) / ss},
+                         "plain": {"p50_ms": float(np.percentile(lp, 50)), "p99_ms": float(np.percentile(lp, 99)),
+                                   "throughput_req_per_s": len(reqs) / sp}}
+    if rank != 0:
+        return 0
+    mid = loads["0.8"]
+    line = {"metric": "p99 request latency at 0.8 x plain capacity (served vs sequential plain)",
+            "value": mid["served"]["p99_ms"], "unit": "ms", "n_gpus": world, "steps": len(reqs), "warmup": 0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "serving: R-MAT scale %d + 32 hubs of out/in degree %d, %d requests (50%% counts of "
+                                   "triangle/diamond/4-clique, 50%% update batches of 1e3-1e5 edges), Poisson arrivals"
+                                   % (scale, args.hub_degree, len(reqs)),
+                       "plain_capacity_req_per_s": capacity, "loads": loads},
+            "plain_p99_ms": mid["plain"]["p99_ms"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -422,7 +546,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="0 skips the CPU baseline")
     ap.add_argument("--scale", type=int, default=SCALE, help="R-MAT scale (profiling runs use smaller ones)")
     ap.add_argument("--queries", default=",".join(BENCH_QUERIES))
-    ap.add_argument("--workload", default="static", choices=["static", "delta"])
+    ap.add_argument("--workload", default="static", choices=["static", "delta", "serve"])
+    ap.add_argument("--requests", type=int, default=120, help="serve workload: requests in the trace")
+    ap.add_argument("--hub-degree", type=int, default=8192, help="serve workload: planted hub degree")
     ap.add_argument("--batch-sizes", default="1000,10000,100000", help="delta workload")
     ap.add_argument("--batches", type=int, default=20, help="delta workload: timed batches per size")
     args = ap.parse_args()
@@ -434,6 +560,8 @@ def main():
         return run_reference(args)
     if args.workload == "delta":
         return run_delta(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 
