@@ -79,11 +79,16 @@ enum {
     GJ_ENGINE_FUSED = 1
 };
 
+/* Option flags. GJ_FLAG_DELTA_FUSED: evaluate the delta queries of update
+ * batches with the fused engine instead of the level-synchronous one (the
+ * default, which spreads a small batch's large fan-out over the whole GPU). */
+enum { GJ_FLAG_DELTA_FUSED = 1 };
+
 typedef struct {
     uint64_t prefix_buffer_bytes; /* cap on device prefix buffers of one evaluation; 0 = 512 MiB */
     uint64_t window;              /* plain engine: candidates per propose+intersect launch; 0 = from the cap */
     uint32_t engine;              /* default engine of gj_count (GJ_ENGINE_*) */
-    uint32_t flags;               /* reserved, 0 */
+    uint32_t flags;               /* GJ_FLAG_* */
     void* stream;                 /* cudaStream_t for all launches; NULL = the context creates one */
 } gj_options;
 

@@ -365,29 +365,10 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeltaBuf buf;
     int rc = gj_delta_prepare(ctx, g, src, dst, sign, b, &buf);
-    gj_work_stats sum{};
-    for (uint32_t qi = 0; qi < nq && rc == GJ_OK; qi++) {
-        const gj_query* q = qs[qi];
-        int64_t c = 0;
-        uint64_t h = 0;
-        for (uint32_t i = 0; i < q->natoms && rc == GJ_OK && buf.batch.n; i++) {
-            int64_t ci = 0;
-            uint64_t hi = 0;
-            rc = gj_engine_plain_plan(ctx, g, q->dplan[i], 0, UINT32_MAX, &buf.batch, &ci, &hi, nullptr, 0, nullptr);
-            c += ci;
-            h += hi;
-            const gj_work_stats& w = ctx->work;
-            sum.seeds += w.seeds;
-            for (int j = 0; j < 9; j++) {
-                sum.extended[j] += w.extended[j];
-                sum.nbind[j] += w.nbind[j];
-                sum.proposals[j] += w.proposals[j];
-                sum.produced[j] += w.produced[j];
-            }
-        }
-        delta_count[qi] = c;
-        delta_checksum[qi] = h;
-    }
+    if (rc == GJ_OK) rc = gj_delta_eval(ctx, g, buf.batch, qs, nq,
+                                         (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN,
+                                         delta_count, delta_checksum);
+    gj_work_stats sum = ctx->work;
     const uint64_t changes = buf.batch.n;
     if (rc == GJ_OK) rc = gj_delta_commit(ctx, g, buf.batch);
     gj_delta_free(ctx, &buf);
@@ -398,6 +379,58 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
     }
     return rc;
 }
+
+}  // extern "C"
+
+int gj_delta_eval(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const gj_query* const* qs, uint32_t nq,
+                  uint32_t engine, int64_t* counts, uint64_t* checksums) {
+    for (uint32_t qi = 0; qi < nq; qi++) {
+        counts[qi] = 0;
+        checksums[qi] = 0;
+    }
+    memset(&ctx->work, 0, sizeof(ctx->work));
+    if (batch.n == 0 || nq == 0) return GJ_OK;
+    if (engine == GJ_ENGINE_FUSED) {
+        std::vector<Plan> plans;
+        std::vector<uint32_t> owner;
+        for (uint32_t qi = 0; qi < nq; qi++)
+            for (uint32_t i = 0; i < qs[qi]->natoms; i++) {
+                plans.push_back(qs[qi]->dplan[i]);
+                owner.push_back(qi);
+            }
+        std::vector<int64_t> c(plans.size());
+        std::vector<uint64_t> h(plans.size());
+        GJ_TRY(gj_engine_fused_delta(ctx, g, batch, plans.data(), (uint32_t)plans.size(), c.data(), h.data()));
+        for (size_t p = 0; p < plans.size(); p++) {
+            counts[owner[p]] += c[p];
+            checksums[owner[p]] += h[p];
+        }
+        return GJ_OK;
+    }
+    gj_work_stats sum{};
+    for (uint32_t qi = 0; qi < nq; qi++) {
+        const gj_query* q = qs[qi];
+        for (uint32_t i = 0; i < q->natoms; i++) {
+            int64_t ci = 0;
+            uint64_t hi = 0;
+            GJ_TRY(gj_engine_plain_plan(ctx, g, q->dplan[i], 0, UINT32_MAX, &batch, &ci, &hi, nullptr, 0, nullptr));
+            counts[qi] += ci;
+            checksums[qi] += hi;
+            const gj_work_stats& w = ctx->work;
+            sum.seeds += w.seeds;
+            for (int j = 0; j < 9; j++) {
+                sum.extended[j] += w.extended[j];
+                sum.nbind[j] += w.nbind[j];
+                sum.proposals[j] += w.proposals[j];
+                sum.produced[j] += w.produced[j];
+            }
+        }
+    }
+    ctx->work = sum;
+    return GJ_OK;
+}
+
+extern "C" {
 
 int gj_graph_last_batch(const gj_graph* g, uint64_t* changes) {
     if (!g || !changes) return GJ_E_INVALID;

@@ -134,7 +134,17 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
         k_scatter_unique<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag, pos, vb, out->nbr, out->key);
         GJ_LAUNCHED(ctx);
     }
-    k_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(out->key, (uint64_t)mu, n, out->off);
+    GJ_TRY(gj_csr_finish(ctx, n, (uint64_t)mu, out));
+    *mu_out = (uint64_t)mu;
+    return GJ_OK;
+}
+
+}  // namespace
+
+int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out) {
+    cudaStream_t st = ctx->stream;
+    if (!out->off) GJ_CUDA_TRY(ctx, cudaMalloc(&out->off, sizeof(int64_t) * ((size_t)n + 1)));
+    k_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(out->key, mu, n, out->off);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     // hash sets of the long lists
@@ -154,16 +164,12 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
     if (tsz > 0) {
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(out->tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
-        k_tab_insert<<<grid_for(ctx, mu), 256, 0, st>>>(out->off, out->nbr, out->key, (uint64_t)mu, out->tab_off,
-                                                         out->tab);
+        k_tab_insert<<<grid_for(ctx, mu), 256, 0, st>>>(out->off, out->nbr, out->key, mu, out->tab_off, out->tab);
         GJ_LAUNCHED(ctx);
     }
     GJ_CUDA_TRY(ctx, cudaGetLastError());
-    *mu_out = (uint64_t)mu;
     return GJ_OK;
 }
-
-}  // namespace
 
 int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m, uint32_t n, gj_graph* g) {
     cudaStream_t st = ctx->stream;

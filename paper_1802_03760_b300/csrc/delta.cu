@@ -122,13 +122,65 @@ __global__ void k_rev_keys(const uint32_t* __restrict__ src, const uint32_t* __r
     }
 }
 
-// flag[e] = 1 if forward slot e survives the batch's deletions.
-__global__ void k_keep_slots(GraphView G, uint64_t m, DeltaSide del, uint32_t* __restrict__ flag) {
+// Records, for every run of equal keys in a key-sorted array, the run's
+// [lo, hi) in the vertex's hash-map entry (field 0: inserts, 1: deletes).
+__global__ void k_range_map(const uint32_t* __restrict__ key, uint32_t n, int which, uint32_t* __restrict__ hkey,
+                            uint4* __restrict__ hval, uint32_t bits) {
+    const uint32_t mask = (1u << bits) - 1u;
+    GRID_STRIDE(p, n) {
+        const uint32_t v = key[p];
+        if (p > 0 && key[p - 1] == v) continue;
+        uint32_t hi = (uint32_t)p + 1;
+        while (hi < n && key[hi] == v) hi++;
+        uint32_t h = gj_tab_home(v, bits);
+        for (uint32_t probe = 0; probe <= mask; probe++) {
+            const uint32_t old = atomicCAS(hkey + h, GJ_EMPTY, v);
+            if (old == GJ_EMPTY || old == v) break;
+            h = (h + 1u) & mask;
+        }
+        if (which == 0) {
+            hval[h].x = (uint32_t)p;
+            hval[h].y = hi;
+        } else {
+            hval[h].z = (uint32_t)p;
+            hval[h].w = hi;
+        }
+    }
+}
+
+// flag[e] = 1 if index slot e (owner key[e], neighbour nbr[e]) survives the
+// batch's deletions in that direction.
+__global__ void k_keep_slots(const uint32_t* __restrict__ key, const uint32_t* __restrict__ nbr, uint64_t m,
+                             DeltaSide side, uint32_t* __restrict__ flag) {
     GRID_STRIDE(e, m) {
-        const uint32_t u = G.fk[e], v = G.fn[e];
-        uint32_t lo, hi;
-        gj_key_range(del.del_key, del.ndel, u, lo, hi);
-        flag[e] = gj_contains(del.del_nbr + lo, hi - lo, v) ? 0u : 1u;
+        const uint32_t u = key[e], v = nbr[e];
+        const uint4 r = gj_delta_ranges(side, u);
+        flag[e] = gj_contains(side.del_nbr + r.z, r.w - r.z, v) ? 0u : 1u;
+    }
+}
+
+// Merges two (owner, neighbour)-sorted slot lists without common pairs: each
+// element's output position is its own index plus the number of elements of
+// the other list that sort before it.
+__global__ void k_merge_slots(const uint32_t* __restrict__ ak, const uint32_t* __restrict__ an, uint64_t na,
+                              const uint32_t* __restrict__ bk, const uint32_t* __restrict__ bn, uint64_t nb,
+                              uint32_t* __restrict__ ok, uint32_t* __restrict__ on) {
+    GRID_STRIDE(i, na + nb) {
+        const bool in_a = i < na;
+        const uint64_t j = in_a ? i : i - na;
+        const uint32_t k = in_a ? ak[j] : bk[j];
+        const uint32_t x = in_a ? an[j] : bn[j];
+        const uint64_t key = ((uint64_t)k << 32) | x;
+        const uint32_t* ok_ = in_a ? bk : ak;
+        const uint32_t* on_ = in_a ? bn : an;
+        uint64_t lo = 0, hi = in_a ? nb : na;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            const uint64_t mk = ((uint64_t)ok_[mid] << 32) | on_[mid];
+            if (mk < key) lo = mid + 1; else hi = mid;
+        }
+        ok[j + lo] = k;
+        on[j + lo] = x;
     }
 }
 
@@ -184,7 +236,11 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
                      uint64_t b, DeltaBuf* out) {
     cudaStream_t st = ctx->stream;
     const uint64_t bb = b ? b : 1;
-    const size_t bytes = 120 * bb + 64 * 256;
+    // vertex -> range maps: at most nd distinct vertices per direction, 2x slots
+    uint32_t mbits = 1;
+    while ((1ull << mbits) < 2 * bb) mbits++;
+    const size_t map_bytes = 2 * ((size_t)4 << mbits) + 2 * ((size_t)16 << mbits);
+    const size_t bytes = 120 * bb + map_bytes + 72 * 256;
     GJ_CUDA_TRY(ctx, cudaMallocAsync(&out->mem, bytes, st));
     Arena A{(char*)out->mem, 0, bytes};
     const uint32_t* d_src = src;
@@ -223,6 +279,10 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
     uint32_t* r_in = (uint32_t*)A.take(4 * bb);
     uint32_t* r_dk = (uint32_t*)A.take(4 * bb);
     uint32_t* r_dn = (uint32_t*)A.take(4 * bb);
+    uint32_t* f_hk = (uint32_t*)A.take((size_t)4 << mbits);
+    uint4* f_hv = (uint4*)A.take((size_t)16 << mbits);
+    uint32_t* r_hk = (uint32_t*)A.take((size_t)4 << mbits);
+    uint4* r_hv = (uint4*)A.take((size_t)16 << mbits);
     uint32_t* err = (uint32_t*)A.take(256);
     if (!err) {
         gj_set_error(ctx, GJ_E_NOMEM, "update batch arena too small");
@@ -289,6 +349,27 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
     R.ins_nbr = r_in;
     R.del_key = r_dk;
     R.del_nbr = r_dn;
+    // vertex -> (insert range, delete range) maps of both directions
+    uint32_t hb = 1;
+    while ((1ull << hb) < 2ull * (uint64_t)nd) hb++;
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(f_hk, 0xff, (size_t)4 << hb, st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(r_hk, 0xff, (size_t)4 << hb, st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(f_hv, 0, (size_t)16 << hb, st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(r_hv, 0, (size_t)16 << hb, st));
+    struct Side { DeltaSide* S; uint32_t* hk; uint4* hv; };
+    for (Side sd : {Side{&F, f_hk, f_hv}, Side{&R, r_hk, r_hv}}) {
+        if (sd.S->nins) {
+            k_range_map<<<grid_for(ctx, sd.S->nins), 256, 0, st>>>(sd.S->ins_key, sd.S->nins, 0, sd.hk, sd.hv, hb);
+            GJ_LAUNCHED(ctx);
+        }
+        if (sd.S->ndel) {
+            k_range_map<<<grid_for(ctx, sd.S->ndel), 256, 0, st>>>(sd.S->del_key, sd.S->ndel, 1, sd.hk, sd.hv, hb);
+            GJ_LAUNCHED(ctx);
+        }
+        sd.S->hkey = sd.hk;
+        sd.S->hval = sd.hv;
+        sd.S->hbits = hb;
+    }
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     return GJ_OK;
 }
@@ -299,42 +380,58 @@ void gj_csr_release(gj_csr& c) {
     c = gj_csr{};
 }
 
+namespace {
+
+// The next version of one index: the committed slots minus the batch's
+// deletions, merged with its (sorted) inserts, then offsets and hash sets.
+int commit_side(gj_ctx* ctx, uint32_t n, const gj_csr& cur, uint64_t m, const DeltaSide& side, gj_csr* out,
+                uint64_t* m_out) {
+    cudaStream_t st = ctx->stream;
+    const uint64_t mm = m ? m : 1;
+    const uint64_t m2 = m - side.ndel + side.nins;
+    char* mem = nullptr;
+    const size_t bytes = 4 * mm + 8 * (mm + 1) + 8 * mm + 4 * 256;
+    GJ_CUDA_TRY(ctx, cudaMallocAsync(&mem, bytes, st));
+    Arena A{mem, 0, bytes};
+    uint32_t* flag = (uint32_t*)A.take(4 * mm);
+    int64_t* pos = (int64_t*)A.take(8 * (mm + 1));
+    uint32_t* kk = (uint32_t*)A.take(4 * mm);
+    uint32_t* kn = (uint32_t*)A.take(4 * mm);
+    uint32_t kept = 0;
+    int rc = GJ_OK;
+    if (m) {
+        k_keep_slots<<<grid_for(ctx, m), 256, 0, st>>>(cur.key, cur.nbr, m, side, flag);
+        GJ_LAUNCHED(ctx);
+        rc = compact_pairs(ctx, nullptr, cur.key, cur.nbr, m, 0, flag, pos, kk, kn, &kept);
+    }
+    if (rc == GJ_OK && cudaMalloc(&out->key, 4 * (size_t)(m2 ? m2 : 1)) != cudaSuccess) rc = GJ_E_NOMEM;
+    if (rc == GJ_OK && cudaMalloc(&out->nbr, 4 * (size_t)(m2 ? m2 : 1)) != cudaSuccess) rc = GJ_E_NOMEM;
+    if (rc == GJ_OK && (uint64_t)kept + side.nins > 0) {
+        k_merge_slots<<<grid_for(ctx, kept + side.nins), 256, 0, st>>>(kk, kn, kept, side.ins_key, side.ins_nbr,
+                                                                      side.nins, out->key, out->nbr);
+        GJ_LAUNCHED(ctx);
+    }
+    cudaFreeAsync(mem, st);
+    if (rc == GJ_OK) rc = gj_csr_finish(ctx, n, m2, out);
+    *m_out = m2;
+    return rc;
+}
+
+}  // namespace
+
 int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_fwd, gj_csr* old_rev) {
     cudaStream_t st = ctx->stream;
     if (d.n == 0) {
         g->version++;
         return GJ_OK;
     }
-    const uint64_t m = g->m;
-    const uint64_t m2 = m - d.view.fwd.ndel + d.view.fwd.nins;
-    const uint64_t mm = m ? m : 1;
-    char* mem = nullptr;
-    const size_t bytes = 4 * mm + 8 * (mm + 1) + 8 * (m2 + 1) + 4 * 256;
-    GJ_CUDA_TRY(ctx, cudaMallocAsync(&mem, bytes, st));
-    Arena A{mem, 0, bytes};
-    uint32_t* flag = (uint32_t*)A.take(4 * mm);
-    int64_t* pos = (int64_t*)A.take(8 * (mm + 1));
-    uint32_t* nsrc = (uint32_t*)A.take(4 * (m2 + 1));
-    uint32_t* ndst = (uint32_t*)A.take(4 * (m2 + 1));
-    const GraphView G = g->view();
-    uint32_t kept = 0;
-    int rc = GJ_OK;
-    if (m) {
-        k_keep_slots<<<grid_for(ctx, m), 256, 0, st>>>(G, m, d.view.fwd, flag);
-        GJ_LAUNCHED(ctx);
-        rc = compact_pairs(ctx, nullptr, g->fwd.key, g->fwd.nbr, m, 0, flag, pos, nsrc, ndst, &kept);
-    }
-    if (rc == GJ_OK && d.view.fwd.nins) {
-        cudaMemcpyAsync(nsrc + kept, d.view.fwd.ins_key, 4ull * d.view.fwd.nins, cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(ndst + kept, d.view.fwd.ins_nbr, 4ull * d.view.fwd.nins, cudaMemcpyDeviceToDevice, st);
-    }
-    gj_graph fresh;
-    fresh.ctx = ctx;
-    if (rc == GJ_OK) rc = gj_csr_build(ctx, nsrc, ndst, (uint64_t)kept + d.view.fwd.nins, g->n, &fresh);
-    cudaFreeAsync(mem, st);
+    gj_csr nf, nr;
+    uint64_t mf = 0, mr = 0;
+    int rc = commit_side(ctx, g->n, g->fwd, g->m, d.view.fwd, &nf, &mf);
+    if (rc == GJ_OK) rc = commit_side(ctx, g->n, g->rev, g->m, d.view.rev, &nr, &mr);
     if (rc != GJ_OK) {
-        gj_csr_release(fresh.fwd);
-        gj_csr_release(fresh.rev);
+        gj_csr_release(nf);
+        gj_csr_release(nr);
         return rc;
     }
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -345,9 +442,9 @@ int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_f
         gj_csr_release(g->fwd);
         gj_csr_release(g->rev);
     }
-    g->fwd = fresh.fwd;
-    g->rev = fresh.rev;
-    g->m = fresh.m;
+    g->fwd = nf;
+    g->rev = nr;
+    g->m = mf;
     g->version++;
     return GJ_OK;
 }

@@ -34,6 +34,8 @@ struct FusedArgs {
     unsigned long long* counts; // [nq]
     unsigned long long* chks;   // [nq]
     unsigned long long* stats;  // [5 * 9] extended, nbind, proposals, produced, seeds; may be null
+    DeltaView D;                // delta plans: the batch's per-direction insert/delete arrays
+    DeltaBatch B;               // delta plans: the batch's signed changes (the seeds)
 };
 
 // Shared-memory layout of one warp (identical on host and device): the
@@ -46,17 +48,28 @@ constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
 constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC;  // mptr + cs + hpre + minb
-__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j) {
-    // sum over i = 2..j-1 of (FC * i * 4 + LVL_FIXED)
-    return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + LVL_FIXED * (j - 2);
+// Delta plans also keep, per prefix, the new-version parts of the min list
+// (inserts, deletes, committed length) and the seed's sign.
+constexpr uint32_t LVL_DELTA = FC * 8 + FC * 8 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
+__host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d) { return LVL_FIXED + (d ? ALIGN16(LVL_DELTA) : 0); }
+__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d = false) {
+    // sum over i = 2..j-1 of (FC * i * 4 + fixed part)
+    return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + lvl_size_fixed(d) * (j - 2);
 }
-__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j) { return lvl_base(j); }
-__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j) { return lvl_base(j) + FC * 4 * j; }
-__host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j) { return off_mptr(j) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j) { return off_cs(j) + ALIGN16((FC + 1) * 8); }
-__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j) { return off_hpre(j) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax) {
-    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : lvl_base(kmax);
+__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d = false) { return lvl_base(j, d); }
+__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d = false) { return lvl_base(j, d) + FC * 4 * j; }
+__host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j, bool d = false) { return off_mptr(j, d) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j, bool d = false) {
+    return off_cs(j, d) + ALIGN16((FC + 1) * 8);
+}
+__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d = false) { return off_hpre(j, d) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j) { return off_minb(j, true) + FC; }
+__host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j) { return off_dins(j) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j) { return off_ddel(j) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j) { return off_dblen(j) + FC * 4; }
+__host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j) { return off_dndel(j) + FC * 4; }
+__host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d = false) {
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : lvl_base(kmax, d);
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
@@ -126,12 +139,16 @@ __device__ __forceinline__ void tab_member2(const uint32_t* __restrict__ tab, ui
     k1 = r1;
 }
 
+// DELTA: every plan is a delta query dQ_i (Section 3.3.1): seeds are the
+// batch's signed changes, atoms read the old or the new version, and each
+// prefix carries its seed's sign into the counts and checksums.
+template <bool DELTA>
 __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t lt = gj_lanemask_lt();
-    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes(A.kmax);
+    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes(A.kmax, DELTA);
     Plan& P = *reinterpret_cast<Plan*>(ws);
     uint64_t* n_ = reinterpret_cast<uint64_t*>(ws + PLAN_BYTES);
     uint64_t* cur_ = n_ + GJ_MAX_K;
@@ -142,6 +159,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
 
     if (lane < GJ_MAX_K) { n_[lane] = 0; cur_[lane] = 0; tot_[lane] = 0; ip_[lane] = 0; }
     __syncwarp();
+    const DeltaView* Dv = DELTA ? &A.D : nullptr;
 
     int cur_q = -1;
     uint32_t k = 0;
@@ -165,11 +183,11 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     // the new one in query order (the tuple hash is a left fold).
     auto activate = [&](int j) {
         const uint32_t nj = (uint32_t)n_[j];
-        uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j));
-        const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j));
-        uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j));
-        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j));
-        uint8_t* minb = ws + off_minb(j);
+        uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j, DELTA));
+        const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j, DELTA));
+        uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j, DELTA));
+        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j, DELTA));
+        uint8_t* minb = ws + off_minb(j, DELTA);
         const bool last = (j == (int)k - 1);
         const uint32_t a_new = P.order[j];
         uint64_t len2[2];
@@ -181,15 +199,37 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 best = ~0ull;
                 uint32_t bi = 0;
                 const uint32_t* bp = nullptr;
-                for (uint32_t b = 0; b < P.nb[j]; b++) {
-                    uint32_t v = tup[P.bpos[j][b] * FC + i];
-                    const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
-                    int64_t s = __ldg(off + v);
-                    uint64_t len = (uint64_t)(__ldg(off + v + 1) - s);
-                    if (len < best) {
-                        best = len;
-                        bi = b;
-                        bp = (P.bdir[j][b] ? G.rn : G.fn) + s;
+                if (DELTA) {
+                    // min by the degree in each atom's version; the list's
+                    // enumeration space also holds the batch's deletions
+                    uint32_t bdeg = 0xffffffffu;
+                    ViewList bl{};
+                    for (uint32_t b = 0; b < P.nb[j]; b++) {
+                        const uint32_t v = tup[P.bpos[j][b] * FC + i];
+                        const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], v);
+                        if (L.degree() < bdeg) {
+                            bdeg = L.degree();
+                            bl = L;
+                            bi = b;
+                        }
+                    }
+                    best = bl.space();
+                    bp = bl.base;
+                    reinterpret_cast<const uint32_t**>(ws + off_dins(j))[i] = bl.ins;
+                    reinterpret_cast<const uint32_t**>(ws + off_ddel(j))[i] = bl.del;
+                    reinterpret_cast<uint32_t*>(ws + off_dblen(j))[i] = bl.base_len;
+                    reinterpret_cast<uint32_t*>(ws + off_dndel(j))[i] = bl.ndel;
+                } else {
+                    for (uint32_t b = 0; b < P.nb[j]; b++) {
+                        uint32_t v = tup[P.bpos[j][b] * FC + i];
+                        const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
+                        int64_t s = __ldg(off + v);
+                        uint64_t len = (uint64_t)(__ldg(off + v + 1) - s);
+                        if (len < best) {
+                            best = len;
+                            bi = b;
+                            bp = (P.bdir[j][b] ? G.rn : G.fn) + s;
+                        }
                     }
                 }
                 mptr[i] = bp;
@@ -277,13 +317,21 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 stat_add(A.stats, 4, 0, (unsigned long long)(left < SEED_CHUNK ? left : SEED_CHUNK));
             }
             uint32_t x0 = 0, x1 = 0;
+            int8_t sg = 1;
             if (keep) {
                 const int64_t e = A.seed_lo[q] + (int64_t)s;
-                x0 = __ldg((P.seed_dir ? G.rk : G.fk) + e);
-                x1 = __ldg((P.seed_dir ? G.rn : G.fn) + e);
+                if (DELTA) {
+                    x0 = A.B.chg_src[e];
+                    x1 = A.B.chg_dst[e];
+                    sg = A.B.chg_sign[e];
+                } else {
+                    x0 = __ldg((P.seed_dir ? G.rk : G.fk) + e);
+                    x1 = __ldg((P.seed_dir ? G.rn : G.fn) + e);
+                }
                 for (uint32_t f = 0; f < P.nsf && keep; f++) {
                     uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
-                    keep = gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
+                    keep = DELTA ? gj_view_member(G, Dv, 0, P.sf_view[f], u, w)
+                                 : gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
                 }
             }
             if (k == 2) {
@@ -293,18 +341,20 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     uint32_t v1 = P.qpos[1] == 0 ? x0 : x1;
                     h = gj_mix64(h ^ (uint64_t)v0);
                     h = gj_mix64(h ^ (uint64_t)v1);
-                    chk += h;
+                    chk += sg > 0 ? h : 0ull - h;
                 }
-                cnt += __popc(__ballot_sync(0xffffffffu, keep));
+                cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
+                       __popc(__ballot_sync(0xffffffffu, keep && sg < 0));
                 continue;
             }
             uint32_t mask = __ballot_sync(0xffffffffu, keep);
             uint32_t n2 = (uint32_t)n_[2];
             if (keep) {
                 uint32_t slot = n2 + __popc(mask & lt);
-                uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(2));
+                uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(2, DELTA));
                 tup[0 * FC + slot] = x0;
                 tup[1 * FC + slot] = x1;
+                if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(2))[slot] = sg;
             }
             __syncwarp();
             if (lane == 0) {
@@ -330,15 +380,15 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
         if (cur_[j] < tot_[j]) {
             const uint64_t tot = tot_[j];
             const uint32_t nj = (uint32_t)n_[j];
-            const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j));
-            const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j));
-            const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j));
-            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j));
-            const uint8_t* minb = ws + off_minb(j);
+            const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA));
+            const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA));
+            const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j, DELTA));
+            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j, DELTA));
+            const uint8_t* minb = ws + off_minb(j, DELTA);
             const bool last = (j == (int)k - 1);
             const uint32_t nb = P.nb[j];
             const uint32_t a_new = P.order[j];
-            uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1));
+            uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA));
             constexpr int MAXO = 3;  // other binding lists cached for a step-uniform prefix
             const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
             uint32_t ol[MAXO], obits[MAXO];
@@ -349,7 +399,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             bool descend = false;
             while (cur < tot) {
                 while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
-                if (last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
+                if (!DELTA && last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
                     // Last level, next 64 candidates all in prefix ip: two per
                     // lane, with their probes interleaved.
                     if (ip != cached) {
@@ -417,8 +467,33 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     i = lo;
                 }
                 uint32_t e = 0;
-                if (keep) e = __ldg(mptr[i] + (t - cs[i]));
-                if (uni && nb - 1 <= (uint32_t)MAXO) {
+                int8_t sg = 1;
+                if (DELTA) {
+                    if (keep) {
+                        // element r of the min list's new-version enumeration space
+                        const uint32_t r = (uint32_t)(t - cs[i]);
+                        const uint32_t blen = reinterpret_cast<const uint32_t*>(ws + off_dblen(j))[i];
+                        const uint32_t ndel = reinterpret_cast<const uint32_t*>(ws + off_dndel(j))[i];
+                        if (r < blen) {
+                            e = __ldg(mptr[i] + r);
+                            if (ndel)
+                                keep = !gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j))[i], ndel, e);
+                        } else {
+                            e = __ldg(reinterpret_cast<const uint32_t* const*>(ws + off_dins(j))[i] + (r - blen));
+                        }
+                        sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j))[i];
+                        const uint32_t b0 = minb[i];
+                        for (uint32_t b = 0; b < nb && keep; b++) {
+                            if (b == b0) continue;
+                            const uint32_t v = tup[P.bpos[j][b] * FC + i];
+                            keep = gj_view_member(G, Dv, P.bdir[j][b], P.bview[j][b], v, e);
+                        }
+                    }
+                } else if (keep) {
+                    e = __ldg(mptr[i] + (t - cs[i]));
+                }
+                if (DELTA) {
+                } else if (uni && nb - 1 <= (uint32_t)MAXO) {
                     if (ip != cached) {
                         const uint32_t b0 = minb[ip];
                         uint32_t o = 0;
@@ -461,9 +536,13 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     if (keep) {
                         uint64_t h = gj_mix64(hpre[i] ^ (uint64_t)e);
                         for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + i]);
-                        chk += h;
+                        chk += (!DELTA || sg > 0) ? h : 0ull - h;
                     }
-                    cnt += __popc(__ballot_sync(0xffffffffu, keep));
+                    if (DELTA)
+                        cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
+                               __popc(__ballot_sync(0xffffffffu, keep && sg < 0));
+                    else
+                        cnt += __popc(__ballot_sync(0xffffffffu, keep));
                     continue;
                 }
                 const uint32_t mask = __ballot_sync(0xffffffffu, keep);
@@ -471,6 +550,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     const uint32_t slot = nn + __popc(mask & lt);
                     for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
                     nt[j * FC + slot] = e;
+                    if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(j + 1))[slot] = sg;
                 }
                 nn += __popc(mask);
                 if (lane == 0) stat_add(A.stats, 3, j + 1, __popc(mask));
@@ -507,12 +587,19 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
 
 // Seed ranges of each query: slots of the seed index keyed by x0 in [v_lo, v_hi).
 __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint32_t v_lo, uint32_t v_hi,
-                              int64_t* seed_lo, int64_t* seed_n, uint64_t* qbase) {
+                              int64_t* seed_lo, int64_t* seed_n, uint64_t* qbase, uint64_t n_changes = 0) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     uint64_t base = 0;
     for (uint32_t q = 0; q < nq; q++) {
-        const int64_t* off = plans[q].seed_dir ? G.ro : G.fo;
-        int64_t a = off[v_lo], b = off[v_hi];
+        int64_t a, b;
+        if (plans[q].delta) {
+            a = 0;
+            b = (int64_t)n_changes;
+        } else {
+            const int64_t* off = plans[q].seed_dir ? G.ro : G.fo;
+            a = off[v_lo];
+            b = off[v_hi];
+        }
         seed_lo[q] = a;
         seed_n[q] = b - a;
         qbase[q] = base;
@@ -554,12 +641,12 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
     GJ_LAUNCHED(ctx);
     const int smem = gj_fused_smem_bytes(kmax);
     if (smem > 48 * 1024)
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
-    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     *results = counts_d;
@@ -598,15 +685,15 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     const int smem = gj_fused_smem_bytes(kmax);
     static int configured_smem = 0;
     if (smem > 48 * 1024 && smem > configured_smem) {
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         configured_smem = smem;
     }
     int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     gj_timer_begin(ctx);
-    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
     gj_timer_end(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
@@ -710,12 +797,12 @@ int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uin
     GJ_LAUNCHED(ctx);
     const int smem = gj_fused_smem_bytes(kmax);
     if (smem > 48 * 1024)
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused, FW * 32, smem));
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
-    k_fused<<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     static_assert(sizeof(int64_t) == sizeof(unsigned long long), "count width");
@@ -756,4 +843,66 @@ extern "C" int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t
     int rc = count_noalloc(ctx, g, qs, nq, counts, checksums);
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
     return rc;
+}
+
+// Delta queries of one batch on the fused engine: all plans (the dQ_i of
+// every query) share persistent launches of up to 64 plans; warps take 32
+// signed changes at a time from one counter across all plans.
+int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const Plan* plans, uint32_t np,
+                          int64_t* counts, uint64_t* checksums) {
+    cudaStream_t st = ctx->stream;
+    gj_work_stats& W = ctx->work;
+    memset(&W, 0, sizeof(W));
+    const GraphView G = g->view();
+    for (uint32_t c0 = 0; c0 < np; c0 += 64) {
+        const uint32_t nc = (np - c0) < 64 ? (np - c0) : 64u;
+        char* base = nullptr;
+        GJ_TRY(gj_scratch(ctx, 1, gj_fused_async_bytes(nc), (void**)&base));
+        const size_t plan_bytes = ((sizeof(Plan) * nc) + 255) & ~(size_t)255;
+        Plan* d_plans = (Plan*)base;
+        int64_t* seed_lo = (int64_t*)(base + plan_bytes);
+        int64_t* seed_n = seed_lo + nc;
+        uint64_t* qbase = (uint64_t*)(seed_n + nc);
+        unsigned long long* counts_d = (unsigned long long*)(qbase + nc + 1);
+        unsigned long long* chks_d = counts_d + nc;
+        unsigned long long* next = chks_d + nc;
+        unsigned long long* stats = next + 1;
+        uint32_t kmax = 2;
+        for (uint32_t q = 0; q < nc; q++) kmax = plans[c0 + q].k > kmax ? plans[c0 + q].k : kmax;
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, plans + c0, sizeof(Plan) * nc, cudaMemcpyHostToDevice, st));
+        GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + 45), st));
+        k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n);
+        GJ_LAUNCHED(ctx);
+        const int smem = (int)(warp_bytes(kmax, true) * FW);
+        if (smem > 48 * 1024)
+            GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        int per_sm = 0;
+        GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<true>, FW * 32, smem));
+        if (per_sm < 1) per_sm = 1;
+        FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+        A.D = batch.view;
+        A.B = batch;
+        gj_timer_begin(ctx);
+        k_fused<true><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
+        GJ_LAUNCHED(ctx);
+        gj_timer_end(ctx);
+        GJ_CUDA_TRY(ctx, cudaGetLastError());
+        unsigned long long h[2 * 64 + 1 + 45];
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h, counts_d, 8 * (2 * (size_t)nc + 1 + 45), cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        for (uint32_t q = 0; q < nc; q++) {
+            counts[c0 + q] = (int64_t)h[q];
+            checksums[c0 + q] = h[nc + q];
+        }
+        const unsigned long long* s = h + 2 * nc + 1;
+        for (int j = 0; j < 9; j++) {
+            W.extended[j] += (int64_t)s[0 * 9 + j];
+            W.nbind[j] += (int64_t)s[1 * 9 + j];
+            W.proposals[j] += (int64_t)s[2 * 9 + j];
+            W.produced[j] += (int64_t)s[3 * 9 + j];
+        }
+        W.seeds += (int64_t)s[4 * 9 + 0];
+    }
+    GJ_TRY(gj_timer_collect(ctx));
+    return GJ_OK;
 }

@@ -130,6 +130,11 @@ struct DeltaSide {
     const uint32_t* del_key;
     const uint32_t* del_nbr;
     uint32_t ndel;
+    // vertex -> its [ins_lo, ins_hi, del_lo, del_hi) ranges, open addressing
+    // over the vertices the batch touches (keys all ones when empty)
+    const uint32_t* hkey;
+    const uint4* hval;
+    uint32_t hbits;
 };
 
 struct DeltaView {
@@ -217,6 +222,8 @@ int gj_radix_sort_kv(gj_ctx* ctx, uint64_t* keys, uint64_t* ktmp, uint32_t* vals
                      uint64_t** kresult, uint32_t** vresult);
 
 int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m, uint32_t n, gj_graph* g);
+// Offsets and hash sets of an index whose key/nbr arrays (mu sorted slots) are set.
+int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out);
 
 // Engines: count (and checksum) of a query over the matches whose x0 lies in [v_lo, v_hi).
 int gj_engine_plain(gj_ctx* ctx, const gj_graph* g, const gj_query* q, uint32_t v_lo, uint32_t v_hi,
@@ -244,6 +251,13 @@ void gj_delta_free(gj_ctx* ctx, DeltaBuf* d);
 int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_fwd = nullptr,
                     gj_csr* old_rev = nullptr);
 void gj_csr_release(gj_csr& c);
+// Delta queries of a batch on the fused engine: np plans in launches of <= 64.
+int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const Plan* plans, uint32_t np,
+                          int64_t* counts, uint64_t* checksums);
+// Signed change of each query's count and checksum under a normalised
+// batch: the sum over its delta queries dQ_i, on the given engine.
+int gj_delta_eval(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const gj_query* const* qs, uint32_t nq,
+                  uint32_t engine, int64_t* counts, uint64_t* checksums);
 
 // One launch over nq queries; counts/checksums are host arrays of nq.
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
@@ -348,6 +362,20 @@ struct ViewList {
     __device__ uint32_t space() const { return base_len + nins; }
 };
 
+// The batch's insert and delete ranges of vertex v in one direction (empty
+// when the batch does not touch v).
+__device__ __forceinline__ uint4 gj_delta_ranges(const DeltaSide& S, uint32_t v) {
+    if (S.hbits == 0) return make_uint4(0, 0, 0, 0);
+    const uint32_t mask = (1u << S.hbits) - 1u;
+    uint32_t h = gj_tab_home(v, S.hbits);
+    while (true) {
+        const uint32_t k = __ldg(S.hkey + h);
+        if (k == v) return S.hval[h];
+        if (k == GJ_EMPTY) return make_uint4(0, 0, 0, 0);
+        h = (h + 1u) & mask;
+    }
+}
+
 __device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
                                                  uint32_t v) {
     const int64_t* off = dir ? G.ro : G.fo;
@@ -355,13 +383,11 @@ __device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const Delta
     ViewList L{(dir ? G.rn : G.fn) + s, (uint32_t)(__ldg(off + v + 1) - s), nullptr, 0, nullptr, 0};
     if (view == GJ_VIEW_NEW && D) {
         const DeltaSide& S = dir ? D->rev : D->fwd;
-        uint32_t lo, hi;
-        gj_key_range(S.ins_key, S.nins, v, lo, hi);
-        L.ins = S.ins_nbr + lo;
-        L.nins = hi - lo;
-        gj_key_range(S.del_key, S.ndel, v, lo, hi);
-        L.del = S.del_nbr + lo;
-        L.ndel = hi - lo;
+        const uint4 r = gj_delta_ranges(S, v);
+        L.ins = S.ins_nbr + r.x;
+        L.nins = r.y - r.x;
+        L.del = S.del_nbr + r.z;
+        L.ndel = r.w - r.z;
     }
     return L;
 }
@@ -373,11 +399,9 @@ __device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaVi
                                                uint32_t v, uint32_t x) {
     if (view == GJ_VIEW_NEW && D) {
         const DeltaSide& S = dir ? D->rev : D->fwd;
-        uint32_t lo, hi;
-        gj_key_range(S.ins_key, S.nins, v, lo, hi);
-        if (gj_contains(S.ins_nbr + lo, hi - lo, x)) return true;
-        gj_key_range(S.del_key, S.ndel, v, lo, hi);
-        if (gj_contains(S.del_nbr + lo, hi - lo, x)) return false;
+        const uint4 r = gj_delta_ranges(S, v);
+        if (gj_contains(S.ins_nbr + r.x, r.y - r.x, x)) return true;
+        if (gj_contains(S.del_nbr + r.z, r.w - r.z, x)) return false;
     }
     return dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
 }

@@ -241,16 +241,9 @@ bool run_batch(gj_server* S) {
     std::vector<uint64_t> h(nq, 0);
     DeltaBuf buf;
     int rc = gj_delta_prepare(ctx, g, r->src.data(), r->dst.data(), r->sign.data(), r->src.size(), &buf);
-    for (uint32_t qi = 0; qi < nq && rc == GJ_OK && buf.batch.n; qi++) {
-        const gj_query* q = r->qs[qi];
-        for (uint32_t i = 0; i < q->natoms && rc == GJ_OK; i++) {
-            int64_t ci = 0;
-            uint64_t hi = 0;
-            rc = gj_engine_plain_plan(ctx, g, q->dplan[i], 0, UINT32_MAX, &buf.batch, &ci, &hi, nullptr, 0, nullptr);
-            c[qi] += ci;
-            h[qi] += hi;
-        }
-    }
+    if (rc == GJ_OK) rc = gj_delta_eval(ctx, g, buf.batch, r->qs.data(), nq,
+                                         (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN,
+                                         c.data(), h.data());
     Retired rt;
     const uint64_t changes = buf.batch.n;
     if (rc == GJ_OK) rc = gj_delta_commit(ctx, g, buf.batch, &rt.fwd, &rt.rev);

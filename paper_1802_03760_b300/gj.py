@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gj.h")
 
 ENGINE_PLAIN = 0
 ENGINE_FUSED = 1
+FLAG_DELTA_FUSED = 1
 
 ERRORS = {
     -1: "GJ_E_INVALID", -2: "GJ_E_RANGE", -3: "GJ_E_NOMEM", -4: "GJ_E_ADMIT", -5: "GJ_E_TRUNCATED",
@@ -148,9 +149,9 @@ def _check(rc: int, ctx=None):
 
 class Context:
     def __init__(self, device: int = 0, prefix_buffer_bytes: int = 0, window: int = 0, engine: int = ENGINE_FUSED,
-                 stream=None):
+                 stream=None, flags: int = 0):
         self._h = None
-        o = Options(prefix_buffer_bytes, window, engine, 0, ctypes.c_void_p(stream) if stream else None)
+        o = Options(prefix_buffer_bytes, window, engine, flags, ctypes.c_void_p(stream) if stream else None)
         h = _VP()
         _check(lib().gj_create(device, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -15,9 +15,11 @@ M64 = (1 << 64) - 1
 NAMES = sorted(QUERIES)
 
 
-@pytest.fixture(scope="module")
-def ctx():
-    c = gj.Context(0)
+@pytest.fixture(scope="module", params=[0, gj.FLAG_DELTA_FUSED], ids=["level-sync", "fused"])
+def ctx(request):
+    """Delta queries run on the level-synchronous engine unless the context asks
+    for the fused one: both are checked."""
+    c = gj.Context(0, flags=request.param)
     yield c
     c.close()
 
