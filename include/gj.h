@@ -188,6 +188,33 @@ int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t 
  */
 int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t nq, int64_t* counts, uint64_t* checksums);
 
+/* gj_count_many restricted to matches whose first attribute (in each
+ * query's global order) lies in [v_lo, v_hi). */
+int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, uint32_t v_lo,
+                     uint32_t v_hi, int64_t* counts, uint64_t* checksums);
+
+/* Launch settings of a context. */
+typedef struct {
+    uint32_t seed_chunk;           /* fused engine: seeds a warp takes per grab (32..4096, multiple of 32) */
+    uint32_t blocks_per_sm;        /* fused engine: resident blocks per SM, 0 = as many as fit */
+    uint64_t prefix_buffer_bytes;  /* level-synchronous engine: prefix-buffer budget, 0 = 512 MiB */
+    double fused_ms, plain_ms;     /* gj_autotune: the sample's time with the chosen settings */
+} gj_tuning;
+int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
+/* Errors: GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under 1 MiB). */
+int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
+/*
+ * Chooses the context's launch settings by timing the given queries on the
+ * first-attribute range [v_lo, v_hi) of g (a sample of the workload): seeds
+ * per grab in {32, 64, 128, 256} x {all, all but one} resident blocks per SM
+ * for the fused engine, and a prefix-buffer budget in {64 MiB, 256 MiB,
+ * 1 GiB, 2 GiB} up to prefix_cap_bytes (0 = 2 GiB) for the level-synchronous
+ * engine (the memory/runtime trade-off of the paper's batch size). Applies
+ * the fastest settings to g's context and returns them.
+ */
+int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
+                uint32_t v_hi, gj_tuning* out);
+
 /* Work units of the last gj_count, gj_count_ex or gj_count_many call on ctx
  * (summed over queries). */
 int gj_last_work(const gj_ctx* ctx, gj_work_stats* out);

@@ -2,6 +2,7 @@
 // context, graph and query handles, counting, listing and kernel timing.
 #include "gj_internal.cuh"
 
+#include <chrono>
 #include <new>
 
 void gj_set_error(gj_ctx* ctx, int code, const std::string& msg) {
@@ -316,8 +317,8 @@ int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, 
     return rc;
 }
 
-int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
-                  uint64_t* checksums) {
+int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, uint32_t v_lo,
+                     uint32_t v_hi, int64_t* counts, uint64_t* checksums) {
     if (!g || (nq && (!qs || !counts || !checksums)) || engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
     for (uint32_t i = 0; i < nq; i++)
         if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
@@ -325,10 +326,10 @@ int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t 
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
-    if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, 0, UINT32_MAX, counts, checksums);
+    if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, v_lo, v_hi, counts, checksums);
     gj_work_stats sum{};
     for (uint32_t i = 0; i < nq; i++) {
-        GJ_TRY(gj_engine_plain(ctx, g, qs[i], 0, UINT32_MAX, counts + i, checksums + i, nullptr, 0, nullptr));
+        GJ_TRY(gj_engine_plain(ctx, g, qs[i], v_lo, v_hi, counts + i, checksums + i, nullptr, 0, nullptr));
         const gj_work_stats& w = ctx->work;
         sum.seeds += w.seeds;
         for (int j = 0; j < 9; j++) {
@@ -339,6 +340,89 @@ int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t 
         }
     }
     ctx->work = sum;
+    return GJ_OK;
+}
+
+int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
+                  uint64_t* checksums) {
+    return gj_count_many_ex(g, qs, nq, engine, 0, UINT32_MAX, counts, checksums);
+}
+
+int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out) {
+    if (!ctx || !out) return GJ_E_INVALID;
+    memset(out, 0, sizeof(*out));
+    out->seed_chunk = ctx->seed_chunk;
+    out->blocks_per_sm = ctx->blocks_per_sm;
+    out->prefix_buffer_bytes = ctx->opt.prefix_buffer_bytes;
+    return GJ_OK;
+}
+
+int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
+    if (!ctx || !t || t->seed_chunk < 32 || t->seed_chunk > 4096 || t->seed_chunk % 32) return GJ_E_INVALID;
+    if (t->prefix_buffer_bytes && t->prefix_buffer_bytes < (1ull << 20)) return GJ_E_INVALID;
+    ctx->seed_chunk = t->seed_chunk;
+    ctx->blocks_per_sm = t->blocks_per_sm;
+    ctx->opt.prefix_buffer_bytes = t->prefix_buffer_bytes;
+    return GJ_OK;
+}
+
+int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
+                uint32_t v_hi, gj_tuning* out) {
+    if (!g || !qs || !nq || !out) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
+    std::vector<int64_t> c(nq);
+    std::vector<uint64_t> h(nq);
+    auto timed = [&](uint32_t engine, double* ms) -> int {
+        GJ_TRY(gj_count_many_ex(g, qs, nq, engine, v_lo, v_hi, c.data(), h.data()));  // warm
+        auto t0 = std::chrono::steady_clock::now();
+        GJ_TRY(gj_count_many_ex(g, qs, nq, engine, v_lo, v_hi, c.data(), h.data()));
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return GJ_OK;
+    };
+    // fused engine: seeds per grab x resident blocks per SM
+    int per_sm_max = 0;
+    {
+        uint32_t kmax = 2;
+        for (uint32_t i = 0; i < nq; i++) kmax = qs[i]->k > kmax ? qs[i]->k : kmax;
+        per_sm_max = gj_fused_occupancy(ctx, kmax);
+    }
+    double best_f = 1e300;
+    uint32_t best_chunk = 32, best_bps = 0;
+    for (uint32_t chunk : {32u, 64u, 128u, 256u}) {
+        for (int bps : {0, per_sm_max - 1}) {  // 0: as many blocks as fit
+            if (bps < 0) continue;
+            ctx->seed_chunk = chunk;
+            ctx->blocks_per_sm = (uint32_t)bps;
+            double ms = 0;
+            GJ_TRY(timed(GJ_ENGINE_FUSED, &ms));
+            if (ms < best_f) {
+                best_f = ms;
+                best_chunk = chunk;
+                best_bps = (uint32_t)bps;
+            }
+        }
+    }
+    ctx->seed_chunk = best_chunk;
+    ctx->blocks_per_sm = best_bps;
+    // plain engine: prefix-buffer budget, at most prefix_cap_bytes
+    if (!prefix_cap_bytes) prefix_cap_bytes = 2ull << 30;
+    double best_p = 1e300;
+    uint64_t best_bytes = 0;
+    for (uint64_t bytes : {64ull << 20, 256ull << 20, 1ull << 30, 2ull << 30}) {
+        if (bytes > prefix_cap_bytes) continue;
+        ctx->opt.prefix_buffer_bytes = bytes;
+        double ms = 0;
+        GJ_TRY(timed(GJ_ENGINE_PLAIN, &ms));
+        if (ms < best_p) {
+            best_p = ms;
+            best_bytes = bytes;
+        }
+    }
+    if (best_bytes) ctx->opt.prefix_buffer_bytes = best_bytes;
+    GJ_TRY(gj_get_tuning(ctx, out));
+    out->fused_ms = best_f;
+    out->plain_ms = best_bytes ? best_p : 0;
     return GJ_OK;
 }
 

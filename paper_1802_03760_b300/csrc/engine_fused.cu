@@ -20,14 +20,14 @@ namespace {
 constexpr int FC = 64;          // frontier capacity per level per warp (2 B')
 constexpr int FT = 32;          // B': descend once a level holds this many prefixes
 constexpr int FW = 8;           // warps per block
-constexpr int SEED_CHUNK = 32;  // seeds per grab
+constexpr int SEED_CHUNK = 32;  // default seeds per grab (a multiple of 32; tunable per launch)
 
 struct FusedArgs {
     GraphView G;
     const Plan* plans;
     uint32_t nq;
     uint32_t kmax;
-    const uint64_t* qbase;      // [nq + 1] start of each query's seed space (multiples of SEED_CHUNK)
+    const uint64_t* qbase;      // [nq + 1] start of each query's seed space (multiples of chunk)
     const int64_t* seed_lo;     // [nq] first seed slot of each query's seed index
     const int64_t* seed_n;      // [nq] number of seeds
     unsigned long long* next;   // work counter over the concatenated seed spaces
@@ -36,6 +36,7 @@ struct FusedArgs {
     unsigned long long* stats;  // [5 * 9] extended, nbind, proposals, produced, seeds; may be null
     DeltaView D;                // delta plans: the batch's per-direction insert/delete arrays
     DeltaBatch B;               // delta plans: the batch's signed changes (the seeds)
+    uint32_t chunk = SEED_CHUNK;  // seeds a warp takes per grab (multiple of 32)
 };
 
 // Shared-memory layout of one warp (identical on host and device): the
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     int cur_q = -1;
     uint32_t k = 0;
     unsigned long long cnt = 0, chk = 0;  // cnt is kept warp-uniform (ballot counts); chk per lane
-    uint64_t pending = ~0ull;  // a grabbed chunk waiting until the warp's buffers drain
+    uint64_t gpos = 0, gend = 0;  // the warp's grabbed, not yet read part of the seed space
     int depth = 1;             // deepest level being extended; 1 = none (take seeds)
 
     auto flush_q = [&]() {
@@ -270,16 +271,14 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
 
     while (true) {
         if (depth == 1) {
-            // ---------------- take seeds
-            uint64_t g;
-            if (pending != ~0ull) {
-                g = pending;
-                pending = ~0ull;
-            } else {
+            // ---------------- take seeds, 32 at a time from the grabbed range
+            if (gpos >= gend) {
                 unsigned long long t = 0;
-                if (lane == 0) t = atomicAdd(A.next, (unsigned long long)SEED_CHUNK);
-                g = __shfl_sync(0xffffffffu, t, 0);
+                if (lane == 0) t = atomicAdd(A.next, (unsigned long long)A.chunk);
+                gpos = __shfl_sync(0xffffffffu, t, 0);
+                gend = gpos + A.chunk;
             }
+            const uint64_t g = gpos;
             if (g >= space) {
                 if (k > 2 && n_[2] > 0) {
                     activate(2);
@@ -296,8 +295,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             }
             const int q = (int)lo;
             if (q != cur_q) {
-                if (k > 2 && n_[2] > 0) {  // finish the other query's prefixes first
-                    pending = g;
+                if (k > 2 && n_[2] > 0) {  // finish the other query's prefixes first (g is read later)
                     activate(2);
                     depth = 2;
                     continue;
@@ -312,9 +310,10 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             }
             const uint64_t s = g - A.qbase[q] + lane;
             bool keep = (int64_t)s < A.seed_n[q];
+            gpos = g + 32;
             if (lane == 0) {
                 int64_t left = A.seed_n[q] - (int64_t)(g - A.qbase[q]);
-                stat_add(A.stats, 4, 0, (unsigned long long)(left < SEED_CHUNK ? left : SEED_CHUNK));
+                if (left > 0) stat_add(A.stats, 4, 0, (unsigned long long)(left < 32 ? left : 32));
             }
             uint32_t x0 = 0, x1 = 0;
             int8_t sg = 1;
@@ -587,7 +586,8 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
 
 // Seed ranges of each query: slots of the seed index keyed by x0 in [v_lo, v_hi).
 __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint32_t v_lo, uint32_t v_hi,
-                              int64_t* seed_lo, int64_t* seed_n, uint64_t* qbase, uint64_t n_changes = 0) {
+                              int64_t* seed_lo, int64_t* seed_n, uint64_t* qbase, uint64_t n_changes = 0,
+                              uint32_t chunk = SEED_CHUNK) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     uint64_t base = 0;
     for (uint32_t q = 0; q < nq; q++) {
@@ -603,7 +603,7 @@ __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint3
         seed_lo[q] = a;
         seed_n[q] = b - a;
         qbase[q] = base;
-        base += ((uint64_t)(b - a) + SEED_CHUNK - 1) / SEED_CHUNK * SEED_CHUNK;
+        base += ((uint64_t)(b - a) + chunk - 1) / chunk * chunk;
     }
     qbase[nq] = base;
 }
@@ -611,6 +611,22 @@ __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint3
 }  // namespace
 
 int gj_fused_smem_bytes(uint32_t kmax) { return (int)(warp_bytes(kmax) * FW); }
+
+int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax) {
+    const int smem = gj_fused_smem_bytes(kmax);
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    (void)ctx;
+    return per_sm < 1 ? 1 : per_sm;
+}
 
 size_t gj_fused_async_bytes(uint32_t nq) {
     const size_t plan_bytes = ((sizeof(Plan) * nq) + 255) & ~(size_t)255;
@@ -637,15 +653,17 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
     for (uint32_t q = 0; q < nq; q++) kmax = hp[q].k > kmax ? hp[q].k : kmax;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp, sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
-    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase);
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
     const int smem = gj_fused_smem_bytes(kmax);
     if (smem > 48 * 1024)
         GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
+    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    A.chunk = ctx->seed_chunk;
     k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
@@ -679,7 +697,7 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp.data(), sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
     GraphView G = g->view();
-    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase);
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
 
     const int smem = gj_fused_smem_bytes(kmax);
@@ -690,8 +708,10 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     }
     int per_sm = 0;
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
+    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    A.chunk = ctx->seed_chunk;
     gj_timer_begin(ctx);
     k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
@@ -871,7 +891,7 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         for (uint32_t q = 0; q < nc; q++) kmax = plans[c0 + q].k > kmax ? plans[c0 + q].k : kmax;
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, plans + c0, sizeof(Plan) * nc, cudaMemcpyHostToDevice, st));
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + 45), st));
-        k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n);
+        k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n, ctx->seed_chunk);
         GJ_LAUNCHED(ctx);
         const int smem = (int)(warp_bytes(kmax, true) * FW);
         if (smem > 48 * 1024)
@@ -879,7 +899,9 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         int per_sm = 0;
         GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<true>, FW * 32, smem));
         if (per_sm < 1) per_sm = 1;
+        if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
         FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+        A.chunk = ctx->seed_chunk;
         A.D = batch.view;
         A.B = batch;
         gj_timer_begin(ctx);

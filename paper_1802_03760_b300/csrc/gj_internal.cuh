@@ -194,6 +194,8 @@ struct gj_ctx {
     gj_work_stats work{};        // units processed by the last count call
     uint64_t launches = 0;       // kernels launched on this context (host-side count)
     struct gj_server* server = nullptr;  // request loop, while serving
+    uint32_t seed_chunk = 32;    // fused engine: seeds per grab
+    uint32_t blocks_per_sm = 0;  // fused engine: resident blocks per SM, 0 = as many as fit
 };
 
 // Counts one kernel launch of ctx (gj_launch_count reports the total).
@@ -264,6 +266,8 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums);
 int gj_fused_smem_bytes(uint32_t kmax);
 size_t gj_fused_async_bytes(uint32_t nq);
+// Resident blocks per SM of the static fused kernel for queries of up to kmax attributes.
+int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax);
 int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t nq, cudaStream_t st, void* dscratch,
                      unsigned long long** results);
 

@@ -48,6 +48,14 @@ class WorkStats(ctypes.Structure):
                 "proposals": list(self.proposals), "produced": list(self.produced)}
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("seed_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
+                ("prefix_buffer_bytes", ctypes.c_uint64), ("fused_ms", ctypes.c_double), ("plain_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Result(ctypes.Structure):
     _fields_ = [("req_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_uint32),
                 ("nq", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("counts", ctypes.c_int64 * 64),
@@ -85,6 +93,12 @@ _SIGS = {
                                    ctypes.POINTER(WorkStats)]),
     "gj_count_many": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P]),
     "gj_count_noalloc": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, _I64P, _U64P]),
+    "gj_count_many_ex": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.c_uint32, _I64P, _U64P]),
+    "gj_get_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(Tuning)]),
+    "gj_set_tuning": (ctypes.c_int, [_VP, ctypes.POINTER(Tuning)]),
+    "gj_autotune": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_uint32, ctypes.POINTER(Tuning)]),
     "gj_last_work": (ctypes.c_int, [_VP, ctypes.POINTER(WorkStats)]),
     "gj_list": (ctypes.c_int, [_VP, _VP, _U32P, ctypes.c_uint64, _U64P, _I64P, _U64P]),
     "gj_apply_batch": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_uint64, ctypes.POINTER(_VP), ctypes.c_uint32,
@@ -278,13 +292,35 @@ def count(g: Graph, q: Query, engine: int | None = None, v_range=None, stats: bo
     return c.value, h.value
 
 
-def count_many(g: Graph, qs, engine: int = ENGINE_FUSED):
+def count_many(g: Graph, qs, engine: int = ENGINE_FUSED, v_range=None):
     n = len(qs)
     arr = (_VP * n)(*[q._h for q in qs])
     c = np.zeros(n, np.int64)
     h = np.zeros(n, np.uint64)
-    _check(lib().gj_count_many(g._h, arr, n, engine, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
+    if v_range is None:
+        _check(lib().gj_count_many(g._h, arr, n, engine, c.ctypes.data_as(_I64P), h.ctypes.data_as(_U64P)), g.ctx)
+    else:
+        _check(lib().gj_count_many_ex(g._h, arr, n, engine, v_range[0], v_range[1], c.ctypes.data_as(_I64P),
+                                      h.ctypes.data_as(_U64P)), g.ctx)
     return [int(x) for x in c], [int(x) for x in h]
+
+
+def get_tuning(ctx: Context) -> dict:
+    t = Tuning()
+    _check(lib().gj_get_tuning(ctx._h, ctypes.byref(t)), ctx)
+    return t.as_dict()
+
+
+def set_tuning(ctx: Context, seed_chunk: int = 32, blocks_per_sm: int = 0, prefix_buffer_bytes: int = 0):
+    t = Tuning(seed_chunk, blocks_per_sm, prefix_buffer_bytes, 0.0, 0.0)
+    _check(lib().gj_set_tuning(ctx._h, ctypes.byref(t)), ctx)
+
+
+def autotune(g: Graph, qs, v_range, prefix_cap_bytes: int = 2 << 30) -> dict:
+    arr = (_VP * len(qs))(*[q._h for q in qs])
+    t = Tuning()
+    _check(lib().gj_autotune(g._h, arr, len(qs), prefix_cap_bytes, v_range[0], v_range[1], ctypes.byref(t)), g.ctx)
+    return t.as_dict()
 
 
 def count_noalloc(g: Graph, qs):

@@ -209,3 +209,38 @@ QUERIES = {
     "4-clique": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
     "5-clique": (5, [(i, j) for i in range(5) for j in range(i + 1, 5)]),
 }
+
+
+def connected_order(atoms, order) -> bool:
+    """True if the first two attributes of order share an atom and every later
+    attribute shares an atom with an earlier one (the orders the loaders'
+    edge-seeded evaluation accepts)."""
+    pos = {a: i for i, a in enumerate(order)}
+    if not any({pos[s], pos[d]} == {0, 1} for s, d in atoms):
+        return False
+    return all(any((pos[s] == j and pos[d] < j) or (pos[d] == j and pos[s] < j) for s, d in atoms)
+               for j in range(2, len(order)))
+
+
+def mixed_queries(count: int = 64, seed: int = 1):
+    """The batched multi-query workload: the five evaluation shapes (triangle,
+    4-cycle, diamond, 4-clique, 5-clique) in their canonical form, then
+    seeded variants in which every atom's direction flips with probability
+    1/2 and the attribute order is a random connected order. Returns
+    (name, k, atoms, order) tuples."""
+    shapes = ["triangle", "4-cycle", "diamond", "4-clique", "5-clique"]
+    out = [(nm, QUERIES[nm][0], list(QUERIES[nm][1]), list(range(QUERIES[nm][0]))) for nm in shapes]
+    ctr = 0
+    rs = subseed(seed, 31)
+    while len(out) < count:
+        r = uniform(2**62, 64, rs, first=64 * ctr)
+        ctr += 1
+        nm = shapes[int(r[0] % 5)]
+        k, atoms = QUERIES[nm]
+        atoms = [(b, a) if (int(r[1 + t]) & 1) else (a, b) for t, (a, b) in enumerate(atoms)]
+        # a random permutation of the attributes from the remaining draws
+        order = sorted(range(k), key=lambda a: int(r[20 + a]))
+        if not connected_order(atoms, order):
+            continue
+        out.append(("%s-v%d" % (nm, len(out)), k, atoms, order))
+    return out
