@@ -144,7 +144,9 @@ int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_a
                     gj_query** out);
 void gj_query_free(gj_query* q);
 
-/* Count and checksum of the matches of q in the committed graph, default engine. */
+/* Count and checksum of the matches of q in the committed graph, default engine.
+ * GJ_E_TIMEOUT: a bounded wait of the fused engine's work queue expired
+ * (the result is not reported). */
 int gj_count(gj_graph* g, const gj_query* q, int64_t* count, uint64_t* checksum);
 
 /*
@@ -199,9 +201,15 @@ typedef struct {
     uint32_t blocks_per_sm;        /* fused engine: resident blocks per SM, 0 = as many as fit */
     uint64_t prefix_buffer_bytes;  /* level-synchronous engine: prefix-buffer budget, 0 = 512 MiB */
     double fused_ms, plain_ms;     /* gj_autotune: the sample's time with the chosen settings */
+    /* fused engine work donation (the balance step of Section 3.4 at warp
+     * granularity): a warp about to extend a batch of >= 32 new prefixes
+     * hands it to a queue that idle warps take from. 0: only while some warp
+     * is idle (default), 1: whenever a queue slot is free (stress setting),
+     * 2: off. Results never depend on it. */
+    uint32_t donation;
 } gj_tuning;
 int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
-/* Errors: GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under 1 MiB). */
+/* Errors: GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under 1 MiB, donation > 2). */
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
 /*
  * Chooses the context's launch settings by timing the given queries on the

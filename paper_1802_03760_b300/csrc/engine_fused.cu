@@ -22,6 +22,36 @@ constexpr int FT = 32;          // B': descend once a level holds this many pref
 constexpr int FW = 8;           // warps per block
 constexpr int SEED_CHUNK = 32;  // default seeds per grab (a multiple of 32; tunable per launch)
 
+// A batch of up to FC prefixes of one plan and level that a busy warp hands
+// to idle warps (the balance step of Section 3.4 at warp granularity).
+struct Bundle {
+    uint32_t plan, level, n, pad;
+    unsigned long long c_lo, c_hi;  // candidate range of the batch to extend (all: 0, ~0)
+    uint32_t tup[GJ_MAX_K][FC];
+    int8_t sg[FC];
+};
+
+constexpr uint64_t RANGE_SPLIT_MIN = 4096;  // remaining candidates worth splitting off
+
+// Shared state of the donation queue, a bounded ring of bundles in which
+// every slot carries a sequence number (free for ticket t when seq == t,
+// holding ticket t's bundle when seq == t + 1). A giver reserves ticket
+// tail only if its slot is free and never waits; a taker takes ticket head
+// only once it is published and frees the slot for ticket head + cap. idle
+// counts warps without work; the launch ends when every warp is idle and
+// head == tail (only working warps give, so nothing can arrive after that).
+struct DonationQueue {
+    Bundle* b = nullptr;  // null: donation off
+    uint32_t cap = 0;     // power of two
+    unsigned long long* head = nullptr;
+    unsigned long long* tail = nullptr;
+    unsigned long long* seq = nullptr;  // [cap]
+    unsigned int* idle = nullptr;
+    unsigned int* err = nullptr;  // set when the bounded idle wait gives up
+    unsigned int nwarps = 0;
+    unsigned int always = 0;  // 1: give whenever a slot is free (stress setting)
+};
+
 struct FusedArgs {
     GraphView G;
     const Plan* plans;
@@ -37,7 +67,10 @@ struct FusedArgs {
     DeltaView D;                // delta plans: the batch's per-direction insert/delete arrays
     DeltaBatch B;               // delta plans: the batch's signed changes (the seeds)
     uint32_t chunk = SEED_CHUNK;  // seeds a warp takes per grab (multiple of 32)
+    DonationQueue Q;
 };
+
+constexpr uint32_t IDLE_WAIT_LIMIT = 1u << 26;  // iterations of the idle wait before giving up
 
 // Shared-memory layout of one warp (identical on host and device): the
 // plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), then
@@ -140,6 +173,18 @@ __device__ __forceinline__ void tab_member2(const uint32_t* __restrict__ tab, ui
     k1 = r1;
 }
 
+__device__ __forceinline__ unsigned int vload(const unsigned int* p) {
+    return *reinterpret_cast<const volatile unsigned int*>(p);
+}
+
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__global__ void k_queue_init(unsigned long long* seq, uint32_t cap) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += gridDim.x * blockDim.x) seq[i] = i;
+}
+
 // DELTA: every plan is a delta query dQ_i (Section 3.3.1): seeds are the
 // batch's signed changes, atoms read the old or the new version, and each
 // prefix carries its seed's sign into the counts and checksums.
@@ -182,7 +227,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
     // Count step for level j: min-c / min-i per prefix, scan of min-c. At
     // the last level also the hash of each prefix's attributes that precede
     // the new one in query order (the tuple hash is a left fold).
-    auto activate = [&](int j) {
+    auto activate = [&](int j, bool count_stats = true) {
         const uint32_t nj = (uint32_t)n_[j];
         uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j, DELTA));
         const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j, DELTA));
@@ -262,7 +307,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             ip_[j] = 0;
         }
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && count_stats) {
             stat_add(A.stats, 0, j, nj);
             stat_add(A.stats, 1, j, (unsigned long long)nj * P.nb[j]);
             stat_add(A.stats, 2, j, total);
@@ -285,7 +330,83 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                     depth = 2;
                     continue;
                 }
-                break;
+                if (!A.Q.b) break;
+                // No seeds left: take a donated bundle, or wait until every
+                // warp is idle and none is left (bounded wait).
+                const unsigned long long mask = A.Q.cap - 1;
+                long long took = -1;
+                bool idle_marked = false, give_up = false;
+                uint32_t backoff = 64;  // ns; doubles while nothing is published (less polling traffic)
+                for (uint32_t it = 0;; it++) {
+                    long long b = -1;
+                    if (lane == 0) {
+                        const unsigned long long h = vload64(A.Q.head);
+                        if (vload64(A.Q.seq + (h & mask)) == h + 1) {  // published
+                            if (idle_marked) atomicSub(A.Q.idle, 1u);
+                            idle_marked = false;
+                            if (atomicCAS(A.Q.head, h, h + 1) == h) b = (long long)h;
+                        } else if (h == vload64(A.Q.tail)) {  // empty
+                            if (!idle_marked) atomicAdd(A.Q.idle, 1u);
+                            idle_marked = true;
+                            if (vload(A.Q.idle) == A.Q.nwarps && vload64(A.Q.head) == vload64(A.Q.tail)) b = -2;
+                        }
+                    }
+                    b = __shfl_sync(0xffffffffu, b, 0);
+                    idle_marked = __shfl_sync(0xffffffffu, idle_marked, 0);
+                    if (b >= 0) {
+                        took = b;
+                        break;
+                    }
+                    if (b == -2) break;
+                    if (it >= IDLE_WAIT_LIMIT) {
+                        give_up = true;
+                        break;
+                    }
+                    __nanosleep(backoff);
+                    if (backoff < 16384) backoff <<= 1;
+                }
+                if (give_up) {
+                    if (lane == 0) atomicExch(A.Q.err, 1u);
+                    break;
+                }
+                if (took < 0) break;
+                __threadfence();
+                const Bundle& Bd = A.Q.b[took & mask];
+                const int q2 = (int)Bd.plan;
+                if (q2 != cur_q) {
+                    flush_q();
+                    cur_q = q2;
+                    const uint32_t* srcw = reinterpret_cast<const uint32_t*>(A.plans + q2);
+                    uint32_t* dstw = reinterpret_cast<uint32_t*>(&P);
+                    for (uint32_t w = lane; w < sizeof(Plan) / 4; w += 32) dstw[w] = srcw[w];
+                    __syncwarp();
+                    k = P.k;
+                }
+                const uint32_t L = Bd.level, nb_ = Bd.n;
+                uint32_t* tupL = reinterpret_cast<uint32_t*>(ws + off_tup(L, DELTA));
+                for (uint32_t c = 0; c < L; c++)
+                    for (uint32_t i = lane; i < nb_; i += 32) tupL[c * FC + i] = Bd.tup[c][i];
+                if (DELTA)
+                    for (uint32_t i = lane; i < nb_; i += 32) reinterpret_cast<int8_t*>(ws + off_dsg(L))[i] = Bd.sg[i];
+                const unsigned long long c_lo = Bd.c_lo, c_hi = Bd.c_hi;
+                __syncwarp();
+                if (lane == 0) {
+                    n_[L] = nb_;
+                    __threadfence();
+                    atomicExch(A.Q.seq + (took & mask), (unsigned long long)took + A.Q.cap);  // free the slot
+                }
+                __syncwarp();
+                const bool ranged = c_hi != ~0ull;
+                activate((int)L, !ranged);  // a candidate range of a batch already counted by its giver
+                if (ranged) {
+                    if (lane == 0) {
+                        cur_[L] = c_lo;
+                        if (c_hi < tot_[L]) tot_[L] = c_hi;
+                    }
+                    __syncwarp();
+                }
+                depth = (int)L;
+                continue;
             }
             // query owning this chunk: last q with qbase[q] <= g
             uint32_t lo = 0, hi = A.nq;
@@ -377,7 +498,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
         // cached in registers across steps.
         const int j = depth;
         if (cur_[j] < tot_[j]) {
-            const uint64_t tot = tot_[j];
+            uint64_t tot = tot_[j];
             const uint32_t nj = (uint32_t)n_[j];
             const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA));
             const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA));
@@ -397,6 +518,41 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             uint32_t nn = last ? 0u : (uint32_t)n_[j + 1];
             bool descend = false;
             while (cur < tot) {
+                // give the upper half of a long remaining range to an idle warp
+                // (the shared idle counter is read on every 32nd step only)
+                if (A.Q.b && tot - cur >= RANGE_SPLIT_MIN && ((cur >> 5) & 31) == 0) {
+                    bool give = false;
+                    unsigned long long slot = 0;
+                    const uint64_t mid = cur + (((tot - cur) / 2 + 31) & ~31ull);
+                    if (lane == 0 && (A.Q.always || vload(A.Q.idle) > 0u)) {
+                        const unsigned long long t = vload64(A.Q.tail);
+                        if (vload64(A.Q.seq + (t & (A.Q.cap - 1))) == t && atomicCAS(A.Q.tail, t, t + 1) == t) {
+                            slot = t;
+                            give = true;
+                        }
+                    }
+                    give = __shfl_sync(0xffffffffu, give, 0);
+                    if (give) {
+                        slot = __shfl_sync(0xffffffffu, slot, 0);
+                        Bundle& Bd = A.Q.b[slot & (A.Q.cap - 1)];
+                        for (int c = 0; c < j; c++)
+                            for (uint32_t i2 = lane; i2 < nj; i2 += 32) Bd.tup[c][i2] = tup[c * FC + i2];
+                        if (DELTA)
+                            for (uint32_t i2 = lane; i2 < nj; i2 += 32)
+                                Bd.sg[i2] = reinterpret_cast<const int8_t*>(ws + off_dsg(j))[i2];
+                        if (lane == 0) {
+                            Bd.plan = (uint32_t)cur_q;
+                            Bd.level = (uint32_t)j;
+                            Bd.n = nj;
+                            Bd.c_lo = mid;
+                            Bd.c_hi = tot;
+                        }
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicExch(A.Q.seq + (slot & (A.Q.cap - 1)), slot + 1);  // publish
+                        tot = mid;
+                    }
+                }
                 while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
                 if (!DELTA && last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
                     // Last level, next 64 candidates all in prefix ip: two per
@@ -554,6 +710,38 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                 nn += __popc(mask);
                 if (lane == 0) stat_add(A.stats, 3, j + 1, __popc(mask));
                 if (nn >= FT) {
+                    // hand the batch to an idle warp when one is waiting
+                    bool donate = false;
+                    unsigned long long slot = 0;
+                    if (A.Q.b && lane == 0 && (A.Q.always || vload(A.Q.idle) > 0u)) {
+                        const unsigned long long t = vload64(A.Q.tail);
+                        if (vload64(A.Q.seq + (t & (A.Q.cap - 1))) == t && atomicCAS(A.Q.tail, t, t + 1) == t) {
+                            slot = t;
+                            donate = true;
+                        }
+                    }
+                    donate = __shfl_sync(0xffffffffu, donate, 0);
+                    if (donate) {
+                        slot = __shfl_sync(0xffffffffu, slot, 0);
+                        Bundle& Bd = A.Q.b[slot & (A.Q.cap - 1)];
+                        for (int c = 0; c <= j; c++)
+                            for (uint32_t i = lane; i < nn; i += 32) Bd.tup[c][i] = nt[c * FC + i];
+                        if (DELTA)
+                            for (uint32_t i = lane; i < nn; i += 32)
+                                Bd.sg[i] = reinterpret_cast<const int8_t*>(ws + off_dsg(j + 1))[i];
+                        if (lane == 0) {
+                            Bd.plan = (uint32_t)cur_q;
+                            Bd.level = (uint32_t)(j + 1);
+                            Bd.n = nn;
+                            Bd.c_lo = 0;
+                            Bd.c_hi = ~0ull;
+                        }
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0) atomicExch(A.Q.seq + (slot & (A.Q.cap - 1)), slot + 1);  // publish
+                        nn = 0;
+                        continue;
+                    }
                     descend = true;
                     break;
                 }
@@ -561,6 +749,7 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             __syncwarp();
             if (lane == 0) {
                 cur_[j] = cur;
+                tot_[j] = tot;
                 ip_[j] = ip;
                 if (!last) n_[j + 1] = nn;
             }
@@ -611,6 +800,63 @@ __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint3
 }  // namespace
 
 int gj_fused_smem_bytes(uint32_t kmax) { return (int)(warp_bytes(kmax) * FW); }
+
+constexpr uint32_t DONATION_CAP = 16384;  // ring slots (power of two)
+
+// Donation queue in scratch slot 4: ring of DONATION_CAP bundles, counters
+// cleared and slot sequence numbers reset.
+static int donation_queue(gj_ctx* ctx, unsigned int nwarps, DonationQueue* Q) {
+    const size_t bundles = sizeof(Bundle) * (size_t)DONATION_CAP;
+    const size_t seqb = sizeof(unsigned long long) * (size_t)DONATION_CAP;
+    const size_t ctrb = 4 * 256;  // head, tail, idle, err each on its own 256-byte line
+    char* base = nullptr;
+    GJ_TRY(gj_scratch(ctx, 4, bundles + seqb + ctrb + 512, (void**)&base));
+    char* p = base + ((bundles + 255) & ~(size_t)255);
+    unsigned long long* seq = (unsigned long long*)p;
+    unsigned long long* ctr = (unsigned long long*)(p + ((seqb + 255) & ~(size_t)255));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(ctr, 0, ctrb, ctx->stream));
+    k_queue_init<<<64, 256, 0, ctx->stream>>>(seq, DONATION_CAP);
+    GJ_LAUNCHED(ctx);
+    Q->b = (Bundle*)base;
+    Q->cap = DONATION_CAP;
+    Q->head = ctr;
+    Q->tail = ctr + 32;
+    Q->idle = (unsigned int*)(ctr + 64);
+    Q->err = (unsigned int*)(ctr + 96);
+    Q->seq = seq;
+    Q->nwarps = nwarps;
+    Q->always = ctx->donation == 1 ? 1u : 0u;
+    if (ctx->donation == 2) Q->b = nullptr;  // off
+    return GJ_OK;
+}
+
+// With donation on, warps wait for one another at the end of the launch,
+// so every block must be resident at once: a cooperative launch guarantees
+// that (the grid is sized from the occupancy of an idle GPU).
+template <bool DELTA>
+static int launch_fused(gj_ctx* ctx, FusedArgs& A, unsigned grid, int smem, cudaStream_t st) {
+    if (A.Q.b) {
+        void* args[] = {&A};
+        GJ_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_fused<DELTA>, dim3(grid), dim3(FW * 32), args,
+                                                     (size_t)smem, st));
+    } else {
+        k_fused<DELTA><<<grid, FW * 32, smem, st>>>(A);
+        GJ_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    GJ_LAUNCHED(ctx);
+    return GJ_OK;
+}
+
+static int donation_check(gj_ctx* ctx, const DonationQueue& Q) {
+    if (!Q.b) return GJ_OK;
+    unsigned int err = 0;
+    GJ_CUDA_TRY(ctx, cudaMemcpy(&err, Q.err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        gj_set_error(ctx, GJ_E_TIMEOUT, "fused engine: a bounded wait of the work-donation queue expired");
+        return GJ_E_TIMEOUT;
+    }
+    return GJ_OK;
+}
 
 int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax) {
     const int smem = gj_fused_smem_bytes(kmax);
@@ -712,14 +958,15 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     A.chunk = ctx->seed_chunk;
+    const unsigned grid = (unsigned)(ctx->sm_count * per_sm);
+    GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
     gj_timer_begin(ctx);
-    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
-    GJ_LAUNCHED(ctx);
+    GJ_TRY(launch_fused<false>(ctx, A, grid, smem, st));
     gj_timer_end(ctx);
-    GJ_CUDA_TRY(ctx, cudaGetLastError());
     std::vector<unsigned long long> h(2 * (size_t)nq + 1 + 45);
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), counts_d, 8 * h.size(), cudaMemcpyDeviceToHost, st));
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    GJ_TRY(donation_check(ctx, A.Q));
     GJ_TRY(gj_timer_collect(ctx));
     for (uint32_t q = 0; q < nq; q++) {
         counts[q] = (int64_t)h[q];
@@ -904,14 +1151,15 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         A.chunk = ctx->seed_chunk;
         A.D = batch.view;
         A.B = batch;
+        const unsigned grid = (unsigned)(ctx->sm_count * per_sm);
+        GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
         gj_timer_begin(ctx);
-        k_fused<true><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
-        GJ_LAUNCHED(ctx);
+        GJ_TRY(launch_fused<true>(ctx, A, grid, smem, st));
         gj_timer_end(ctx);
-        GJ_CUDA_TRY(ctx, cudaGetLastError());
         unsigned long long h[2 * 64 + 1 + 45];
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h, counts_d, 8 * (2 * (size_t)nc + 1 + 45), cudaMemcpyDeviceToHost, st));
         GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        GJ_TRY(donation_check(ctx, A.Q));
         for (uint32_t q = 0; q < nc; q++) {
             counts[c0 + q] = (int64_t)h[q];
             checksums[c0 + q] = h[nc + q];

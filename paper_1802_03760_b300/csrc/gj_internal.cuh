@@ -185,7 +185,7 @@ struct gj_ctx {
     bool own_stream = false;
     gj_options opt{};
     int sm_count = 0;
-    ScratchArena scratch[4];
+    ScratchArena scratch[6];
     KernelTimer timer;
     uint64_t* d_acc = nullptr;   // small device accumulators (count, checksum, counters)
     uint64_t* h_acc = nullptr;   // pinned host mirror
@@ -196,6 +196,7 @@ struct gj_ctx {
     struct gj_server* server = nullptr;  // request loop, while serving
     uint32_t seed_chunk = 32;    // fused engine: seeds per grab
     uint32_t blocks_per_sm = 0;  // fused engine: resident blocks per SM, 0 = as many as fit
+    uint32_t donation = 0;       // fused engine work donation: 0 when warps idle, 1 always, 2 off
 };
 
 // Counts one kernel launch of ctx (gj_launch_count reports the total).

@@ -31,14 +31,17 @@ def test_64_queries_one_launch(setup):
     ctx, g, qs, want, n = setup
     l0 = ctx.launches
     c, h = gj.count_many(g, qs, engine=gj.ENGINE_FUSED)
-    assert ctx.launches - l0 == 2  # seed ranges + one persistent launch for all 64 queries
+    assert ctx.launches - l0 == 3  # seed ranges, work-queue reset, one persistent launch for all 64 queries
     assert list(zip(c, h)) == want
 
 
-@pytest.mark.parametrize("chunk,bps", [(64, 0), (128, 1), (256, 2), (32, 1)])
-def test_fused_settings_do_not_change_results(setup, chunk, bps):
+@pytest.mark.parametrize("chunk,bps,donation", [(64, 0, 0), (128, 1, 1), (256, 2, 2), (32, 1, 1), (32, 0, 1)])
+def test_fused_settings_do_not_change_results(setup, chunk, bps, donation):
+    """Seeds per grab, blocks per SM and work donation (1 = donate whenever a
+    queue slot is free, which exercises the queue on every descent) must not
+    change any count or checksum."""
     ctx, g, qs, want, n = setup
-    gj.set_tuning(ctx, seed_chunk=chunk, blocks_per_sm=bps)
+    gj.set_tuning(ctx, seed_chunk=chunk, blocks_per_sm=bps, donation=donation)
     try:
         assert list(zip(*gj.count_many(g, qs, engine=gj.ENGINE_FUSED))) == want
     finally:

@@ -188,6 +188,26 @@ def test_count_many_one_launch(ctx):
         assert list(zip(c, h)) == want, eng
 
 
+@pytest.mark.parametrize("donation", [1, 2])
+def test_work_donation_stress(ctx, donation):
+    """Donating every batch of new prefixes to the queue (1) or never (2)
+    gives the same counts as the oracle, including delta-free deep queries."""
+    rng = np.random.default_rng(61)
+    s, d = random_graph(rng, 3000, 60000, recip=0.3)
+    og = oracle.Graph(3000, s, d)
+    g = gj.Graph(ctx, s, d, 3000)
+    names = ["diamond", "4-clique", "5-clique", "4-cycle"]
+    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in names]
+    want = [og.count(oracle.Query(*QUERIES[nm]), mode=1) for nm in names]
+    gj.set_tuning(ctx, donation=donation)
+    try:
+        assert list(zip(*gj.count_many(g, qs, engine=gj.ENGINE_FUSED))) == want
+        for q, w in zip(qs, want):
+            assert gj.count(g, q, engine=gj.ENGINE_FUSED) == w
+    finally:
+        gj.set_tuning(ctx)
+
+
 @pytest.fixture(scope="module")
 def rmat20(ctx):
     s, d = rmat_edges(20, seed=1)
