@@ -250,9 +250,8 @@ def run_ours(args):
     step_ms = sum(times) / len(times)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([step_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+        from paper_1802_03760_b300.shard import max_over_ranks
+        step_ms = max_over_ranks(step_ms)
         dist.barrier()
 
     # end to end through the C ABI with pinned host inputs
@@ -261,10 +260,8 @@ def run_ours(args):
         raise RuntimeError("end-to-end counts differ from the device-resident run")
     e2e_ms = sum(e2e_times) / len(e2e_times)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+        from paper_1802_03760_b300.shard import max_over_ranks
+        e2e_ms = max_over_ranks(e2e_ms)
 
     # the plain level-synchronous engine, one query after another, same workload
     plain = None
