@@ -93,7 +93,7 @@ __global__ void k_tab_insert(const int64_t* __restrict__ off, const uint32_t* __
         const uint32_t mask = (1u << bits) - 1u;
         uint32_t* t = tab + tab_off[v];
         const uint32_t x = nbr[e];
-        uint32_t h = gj_tab_home(x, bits);
+        uint32_t h = gj_tab_start(x, bits);  // first slot of the home group
         for (uint32_t probe = 0; probe <= mask; probe++) {
             if (atomicCAS(t + h, GJ_EMPTY, x) == GJ_EMPTY) break;
             h = (h + 1u) & mask;

@@ -149,25 +149,23 @@ __device__ __forceinline__ void member32x2(const uint32_t* __restrict__ a, uint3
     k1 = k1 && f1 == e1;
 }
 
-// Two membership tests against the same hash set, probes interleaved.
+// Two membership tests against the same hash set (groups of eight slots,
+// as in gj_tab_member), their loads interleaved.
 __device__ __forceinline__ void tab_member2(const uint32_t* __restrict__ tab, uint32_t bits, uint32_t e0, bool& k0,
                                             uint32_t e1, bool& k1) {
     const uint32_t mask = (1u << bits) - 1u;
-    uint32_t h0 = gj_tab_home(e0, bits), h1 = gj_tab_home(e1, bits);
+    uint32_t g0 = gj_tab_start(e0, bits), g1 = gj_tab_start(e1, bits);
     bool a0 = k0, a1 = k1, r0 = false, r1 = false;
     while (a0 || a1) {
-        const uint32_t v0 = a0 ? __ldg(tab + h0) : 0u;
-        const uint32_t v1 = a1 ? __ldg(tab + h1) : 0u;
-        if (a0) {
-            if (v0 == e0) { r0 = true; a0 = false; }
-            else if (v0 == GJ_EMPTY) a0 = false;
-            else h0 = (h0 + 1u) & mask;
-        }
-        if (a1) {
-            if (v1 == e1) { r1 = true; a1 = false; }
-            else if (v1 == GJ_EMPTY) a1 = false;
-            else h1 = (h1 + 1u) & mask;
-        }
+        bool hit0 = false, emp0 = false, hit1 = false, emp1 = false;
+        if (a0) gj_tab_group(tab, g0, e0, hit0, emp0);
+        if (a1) gj_tab_group(tab, g1, e1, hit1, emp1);
+        r0 |= hit0;
+        r1 |= hit1;
+        a0 = a0 && !hit0 && !emp0;
+        a1 = a1 && !hit1 && !emp1;
+        g0 = (g0 + 8u) & mask;
+        g1 = (g1 + 8u) & mask;
     }
     k0 = r0;
     k1 = r1;

@@ -312,16 +312,38 @@ __device__ __forceinline__ uint32_t gj_tab_home(uint32_t e, uint32_t bits) {
     return (e * 0x9e3779b1u) >> (32u - bits);
 }
 
-// Membership of e in a linear-probing hash set (no deletions, never full):
-// probe from the home slot until e or an empty slot.
+// Hash sets are read a group of eight slots (one 32-byte sector) at a time:
+// a set has at least 32 slots, a power of two, and starts on a 128-byte
+// boundary. A key's probe sequence starts at the first slot of its home
+// group and runs slot by slot (linear probing, no deletions, never full),
+// so a key that is not in its home group was inserted only after that
+// group had filled up. Hence, scanning group by group from the home group,
+// a group that holds e answers yes and a group with an empty slot answers
+// no.
+static_assert(GJ_HASH_MIN_DEG >= 4, "a hash set must span whole groups of eight slots");
+__device__ __forceinline__ uint32_t gj_tab_start(uint32_t e, uint32_t bits) { return gj_tab_home(e, bits) & ~7u; }
+
+// Reads group g and compares its slots with e: hit if one holds e, emp if
+// one is empty.
+__device__ __forceinline__ void gj_tab_group(const uint32_t* __restrict__ tab, uint32_t g, uint32_t e, bool& hit,
+                                             bool& emp) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(tab + g));
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(tab + g) + 1);
+    hit = (a.x == e) | (a.y == e) | (a.z == e) | (a.w == e) | (b.x == e) | (b.y == e) | (b.z == e) | (b.w == e);
+    emp = (a.x == GJ_EMPTY) | (a.y == GJ_EMPTY) | (a.z == GJ_EMPTY) | (a.w == GJ_EMPTY) | (b.x == GJ_EMPTY) |
+          (b.y == GJ_EMPTY) | (b.z == GJ_EMPTY) | (b.w == GJ_EMPTY);
+}
+
+// Membership of e in a hash set of 2^bits slots.
 __device__ __forceinline__ bool gj_tab_member(const uint32_t* __restrict__ tab, uint32_t bits, uint32_t e) {
     const uint32_t mask = (1u << bits) - 1u;
-    uint32_t h = gj_tab_home(e, bits);
+    uint32_t g = gj_tab_start(e, bits);
     while (true) {
-        const uint32_t v = __ldg(tab + h);
-        if (v == e) return true;
-        if (v == GJ_EMPTY) return false;
-        h = (h + 1u) & mask;
+        bool hit, emp;
+        gj_tab_group(tab, g, e, hit, emp);
+        if (hit) return true;
+        if (emp) return false;
+        g = (g + 8u) & mask;
     }
 }
 
