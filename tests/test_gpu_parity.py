@@ -209,6 +209,49 @@ def test_work_donation_stress(ctx, donation):
 
 
 @pytest.fixture(scope="module")
+def hub_graph():
+    """H hubs with edges h_i -> h_j (i < j) and h_i -> every vertex of a
+    common set S, plus a sprinkle of random edges; the oracle's counts."""
+    rng = np.random.default_rng(71)
+    n, H, S = 12000, 40, 5000
+    ids = rng.permutation(n).astype(np.uint32)
+    hubs, common = ids[:H], ids[H:H + S]
+    hs, hd = zip(*[(hubs[i], hubs[j]) for i in range(H) for j in range(i + 1, H)])
+    s = np.concatenate([np.array(hs, np.uint32), np.repeat(hubs, S)])
+    d = np.concatenate([np.array(hd, np.uint32), np.tile(common, H)])
+    core = len(s)
+    s = np.concatenate([s, rng.integers(0, n, 20000).astype(np.uint32)])
+    d = np.concatenate([d, rng.integers(0, n, 20000).astype(np.uint32)])
+    names = ["triangle", "4-clique", "diamond"]
+    og = oracle.Graph(n, s, d)
+    want = [og.count(oracle.Query(*QUERIES[nm]), mode=1) for nm in names]
+    return n, H, S, s, d, core, names, want
+
+
+@pytest.mark.parametrize("donation", [0, 1, 2])
+def test_long_lists_split_ranges(ctx, hub_graph, donation):
+    """Every seed prefix has thousands of candidates, so warps split their
+    candidate ranges (range donation) inside prefixes that are not the last
+    of their batch, and the last level runs its long-list steps. Without
+    the random edges the triangle count has the closed form sum over
+    i < j of |S| + H-1-j."""
+    n, H, S, s, d, core, names, want = hub_graph
+    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in names]
+    g0 = gj.Graph(ctx, s[:core], d[:core], n)
+    assert gj.count(g0, qs[0])[0] == sum(S + H - 1 - j for i in range(H) for j in range(i + 1, H))
+    g0.free()
+    g = gj.Graph(ctx, s, d, n)
+    gj.set_tuning(ctx, donation=donation)
+    try:
+        assert list(zip(*gj.count_many(g, qs, engine=gj.ENGINE_FUSED))) == want
+        for q, w in zip(qs, want):
+            assert gj.count(g, q, engine=gj.ENGINE_FUSED) == w
+    finally:
+        gj.set_tuning(ctx)
+        g.free()
+
+
+@pytest.fixture(scope="module")
 def rmat20(ctx):
     s, d = rmat_edges(20, seed=1)
     return s, d, oracle.Graph(1 << 20, s, d), gj.Graph(ctx, s, d, 1 << 20)
