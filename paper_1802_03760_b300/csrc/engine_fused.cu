@@ -187,7 +187,7 @@ __global__ void k_queue_init(unsigned long long* seq, uint32_t cap) {
 // batch's signed changes, atoms read the old or the new version, and each
 // prefix carries its seed's sign into the counts and checksums.
 template <bool DELTA>
-__global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
+__global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -515,10 +515,12 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
             uint32_t ip = (uint32_t)ip_[j];
             uint32_t nn = last ? 0u : (uint32_t)n_[j + 1];
             bool descend = false;
+            uint64_t chk_at = cur;  // the next cursor at which the shared idle counter is read
             while (cur < tot) {
                 // give the upper half of a long remaining range to an idle warp
-                // (the shared idle counter is read on every 32nd step only)
-                if (A.Q.b && tot - cur >= RANGE_SPLIT_MIN && ((cur >> 5) & 31) == 0) {
+                // (the shared idle counter is read once per 1024 candidates)
+                if (A.Q.b && tot - cur >= RANGE_SPLIT_MIN && cur >= chk_at) {
+                    chk_at = cur + 1024;
                     bool give = false;
                     unsigned long long slot = 0;
                     const uint64_t mid = cur + (((tot - cur) / 2 + 31) & ~31ull);
@@ -579,31 +581,44 @@ __global__ void __launch_bounds__(FW * 32) k_fused(FusedArgs A) {
                         }
                         cached = ip;
                     }
-                    const uint64_t t0 = cur + lane, t1 = cur + 32 + lane;
-                    bool k0 = t0 < tot, k1 = t1 < tot;
-                    const uint32_t* ml = mptr[ip];
+                    // Up to 16 steps on prefix ip alone, its invariants in
+                    // registers and 32-bit offsets r into its min list. When
+                    // the warp's range [cur, tot) ends inside prefix ip (its
+                    // batch's last prefix, or a range split off by a
+                    // donation), the last step may be partial.
                     const uint64_t c0 = cs[ip];
-                    const uint32_t e0 = k0 ? __ldg(ml + (t0 - c0)) : 0u;
-                    const uint32_t e1 = k1 ? __ldg(ml + (t1 - c0)) : 0u;
+                    const uint64_t pend = ip + 1 < nj ? cs[ip + 1] : tot;
+                    const bool tail_ok = tot <= pend;
+                    const uint32_t rend = (uint32_t)((tail_ok ? tot : pend) - c0);
+                    const uint32_t* ml = mptr[ip];
+                    const uint64_t hp = hpre[ip];
+                    uint32_t r = (uint32_t)(cur - c0);
+                    uint32_t steps = 0;
+                    do {
+                        const uint32_t q0 = r + lane, q1 = r + 32 + lane;
+                        bool k0 = q0 < rend, k1 = q1 < rend;
+                        const uint32_t e0 = k0 ? __ldg(ml + q0) : 0u;
+                        const uint32_t e1 = k1 ? __ldg(ml + q1) : 0u;
 #pragma unroll
-                    for (int q = 0; q < MAXO; q++) {
-                        if (q + 1 < (int)nb) {
-                            if (obits[q]) tab_member2(ob[q], obits[q], e0, k0, e1, k1);
-                            else member32x2(ob[q], ol[q], e0, k0, e1, k1);
+                        for (int q = 0; q < MAXO; q++) {
+                            if (q + 1 < (int)nb) {
+                                if (obits[q]) tab_member2(ob[q], obits[q], e0, k0, e1, k1);
+                                else member32x2(ob[q], ol[q], e0, k0, e1, k1);
+                            }
                         }
-                    }
-                    if (k0 | k1) {
-                        const uint64_t hp = hpre[ip];
-                        uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
-                        for (uint32_t a = a_new + 1; a < k; a++) {
-                            const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
-                            h0 = gj_mix64(h0 ^ x);
-                            h1 = gj_mix64(h1 ^ x);
+                        if (k0 | k1) {
+                            uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
+                            for (uint32_t a = a_new + 1; a < k; a++) {
+                                const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
+                                h0 = gj_mix64(h0 ^ x);
+                                h1 = gj_mix64(h1 ^ x);
+                            }
+                            chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
                         }
-                        chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
-                    }
-                    cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
-                    cur += 64;
+                        cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                        r += 64;
+                    } while (++steps < 16 && r < rend && (tail_ok || rend - r >= 64));
+                    cur = c0 + r;
                     continue;
                 }
                 const uint64_t t = cur + lane;
