@@ -55,7 +55,7 @@ enum {
     GJ_E_ADMIT = -4,      /* request needs more device memory than the budget allows */
     GJ_E_TRUNCATED = -5,  /* more matches than the output capacity */
     GJ_E_TIMEOUT = -6,    /* a bounded wait expired */
-    GJ_E_OVERFLOW = -7,   /* a count left the int64 range */
+    GJ_E_OVERFLOW = -7,   /* reserved, not returned: counts are exact below 2^63 and not checked for wrap-around */
     GJ_E_CUDA = -8,       /* a CUDA runtime call failed (gj_last_error has the text) */
     GJ_E_PENDING = -9,    /* request not finished yet */
     GJ_E_NOTFOUND = -10   /* unknown request id */
