@@ -2,13 +2,15 @@
 // of each vertex, sorted) and the reverse index (in-neighbours, sorted), the
 // two indices every atom of every query shares (Section 4.1). An index gives
 // an extension set's size in O(1) (offset difference), its contents in
-// linear time (a contiguous sorted run) and membership by binary search
-// (the three properties of Section 2.2).
+// linear time (a contiguous sorted run) and membership by binary search,
+// or by a hash set for lists of at least GJ_HASH_MIN_DEG entries (the
+// three properties of Section 2.2).
 //
 // Steps per index: pack (key vertex, neighbour) into one 64-bit key with
 // self-loops mapped to an all-ones sentinel, radix sort, keep the first of
-// each run of equal keys, scatter neighbours and key vertices, and set
-// off[v] = first slot whose key vertex is >= v.
+// each run of equal keys, scatter neighbours and key vertices, set
+// off[v] = first slot whose key vertex is >= v, then size and fill the
+// hash sets of the long lists.
 #include "gj_internal.cuh"
 
 namespace {

@@ -8,11 +8,17 @@
 // prefix its smallest binding list (min-c, min-i), a warp scan lays their
 // candidates on one line, and every step proposes the next 32 candidates
 // (one per lane, several prefixes per step when lists are short), tests
-// each against the other binding lists by binary search, and ballots the
-// survivors into the next level (or counts and hashes them at the last
-// level). The warp always works on the deepest level with pending work,
-// so memory stays O(k * B') per warp. Warps take 32 seed edges at a time
-// from one counter shared by every query of the launch (work stealing).
+// each against the other binding lists (hash sets for long lists, binary
+// search for short ones), and ballots the survivors into the next level
+// (or counts and hashes them at the last level, two candidates per lane
+// while one prefix's list lasts). The warp always works on the deepest
+// level with pending work, so memory stays O(k * B') per warp.
+//
+// Balance (Section 3.4 at warp granularity): warps take seed chunks (32
+// seed edges by default) from one counter shared by every query of the
+// launch; a warp that fills a level while others are idle hands the batch
+// to a ring of bundles, and a warp with a long remaining candidate range
+// hands over its upper half.
 #include "gj_internal.cuh"
 
 namespace {

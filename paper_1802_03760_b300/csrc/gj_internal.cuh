@@ -44,7 +44,8 @@ void gj_set_error(gj_ctx* ctx, int code, const std::string& msg);
 // nbr; key[e] is the vertex whose list holds slot e (so (key[e], nbr[e]) is
 // an edge of the index, in index order). Lists of at least GJ_HASH_MIN_DEG
 // entries also get an open-addressing hash set in tab (2^ceil(log2(2 len))
-// slots from tab_off[v], empty slots all ones) for constant-time membership.
+// slots from tab_off[v], empty slots all ones, probed in groups of eight
+// slots; see gj_tab_member) for constant-time membership.
 struct gj_csr {
     int64_t* off = nullptr;      // [n + 1]
     uint32_t* nbr = nullptr;     // [m]
