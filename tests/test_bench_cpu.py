@@ -1,0 +1,83 @@
+"""Host logic of bench.py, on the CPU: the reference arm's JSON line (the
+CPU oracle timed on a bounded sample of the benchmark's workload), the
+silence of non-zero ranks under torchrun, and the cost model behind the
+roofline's algorithmic bytes, worked by hand on complete DAGs."""
+import contextlib
+import io
+import json
+import types
+
+import numpy as np
+
+import bench
+import oracle
+from paper_1802_03760_b300.inputs import QUERIES
+
+
+def _args(**kw):
+    a = types.SimpleNamespace(gpus=1, steps=2, warmup=1, impl="reference", scale=10,
+                              queries=list(bench.BENCH_QUERIES))
+    a.__dict__.update(kw)
+    return a
+
+
+def _run_reference(monkeypatch, **env):
+    orig = bench.cpu_sample
+    # a short sample per step; the arm's own sizing gives each step seconds
+    monkeypatch.setattr(bench, "cpu_sample", lambda s, d, n, target, q: orig(s, d, n, 0.05, q))
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    for k, v in env.items():
+        monkeypatch.setenv(k, v)
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        rc = bench.run_reference(_args())
+    return rc, [ln for ln in buf.getvalue().splitlines() if ln.strip()]
+
+
+def test_reference_arm_prints_one_line(monkeypatch):
+    rc, lines = _run_reference(monkeypatch)
+    assert rc == 0 and len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference"
+    assert line["metric"] == bench.METRIC and line["unit"] == "matches/s"
+    assert line["higher_is_better"] is True and line["steps"] == 2 and line["warmup"] == 1
+    assert line["value"] >= 0 and line["config"]["workload"] == bench.workload_name(10, bench.BENCH_QUERIES)
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert "first attribute in [0, " in cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "matches/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_are_silent(monkeypatch):
+    rc, lines = _run_reference(monkeypatch, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    assert rc == 0 and lines == []
+
+
+def _work(n, name):
+    s, d = np.triu_indices(n, 1)
+    og = oracle.Graph(n, s.astype(np.uint32), d.astype(np.uint32))
+    c, _, st = og.count(oracle.Query(*QUERIES[name]), stats=True, mode=1)
+    w = types.SimpleNamespace(seeds=n * (n - 1) // 2, extended=list(st.extended), nbind=list(st.nbind_sum),
+                              proposals=list(st.proposals), produced=list(st.prefixes))
+    return c, w
+
+
+def test_algorithmic_bytes_triangle_on_complete_dag():
+    # DAG on 4 vertices (i -> j for i < j): 6 seed edges (a, b), each extended
+    # by 2 binding lists with min count 3 - b: 2 + 1 + 0 + 1 + 0 + 0 = 4 proposals.
+    c, w = _work(4, "triangle")
+    assert c == 4 and (w.extended[2], w.nbind[2], w.proposals[2]) == (6, 12, 4)
+    assert bench.algorithmic_bytes(w, 3) == 8 * 6 + 4 * 2 * 6 + 16 * 12 + 4 * 4 + 4 * 4 * 1 == 320
+
+
+def test_algorithmic_bytes_4clique_on_complete_dag():
+    # DAG on 6 vertices: 15 seeds with min count 5 - b (20 proposals, 20
+    # triangles written as 3-tuples); 20 triangles (a, b, c) with 3 binding
+    # lists and min count 5 - c (15 proposals, 2 probes each).
+    c, w = _work(6, "4-clique")
+    assert c == 15 and (w.proposals[2], w.produced[3], w.proposals[3]) == (20, 20, 15)
+    level2 = 4 * 2 * 15 + 16 * 30 + 4 * 20 + 4 * 20 * 1 + 4 * 3 * 20
+    level3 = 4 * 3 * 20 + 16 * 60 + 4 * 15 + 4 * 15 * 2
+    assert bench.algorithmic_bytes(w, 4) == 8 * 15 + level2 + level3 == 2500
