@@ -966,11 +966,8 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     GJ_LAUNCHED(ctx);
 
     const int smem = gj_fused_smem_bytes(kmax);
-    static int configured_smem = 0;
-    if (smem > 48 * 1024 && smem > configured_smem) {
+    if (smem > 48 * 1024)  // a per-device attribute: set on every call, as the context's device is current
         GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        configured_smem = smem;
-    }
     int per_sm = 0;
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
     if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
