@@ -105,7 +105,8 @@ typedef struct {
 } gj_work_stats;
 
 /* Creates a context on CUDA device `cuda_device`. opt may be NULL
- * (defaults). Errors: GJ_E_INVALID (bad device or engine), GJ_E_CUDA. */
+ * (defaults). Errors: GJ_E_INVALID (negative or out-of-range device index,
+ * bad engine), GJ_E_CUDA (no usable CUDA driver or device; a failed set-up). */
 int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out);
 void gj_destroy(gj_ctx* ctx);
 const char* gj_strerror(int code);

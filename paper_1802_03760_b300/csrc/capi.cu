@@ -123,11 +123,13 @@ const char* gj_last_error(const gj_ctx* ctx) { return ctx ? ctx->last_error.c_st
 int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
     if (!out) return GJ_E_INVALID;
     *out = nullptr;
+    if (cuda_device < 0) return GJ_E_INVALID;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev) {
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {  // no usable driver or device
         cudaGetLastError();
-        return cuda_device < 0 ? GJ_E_INVALID : GJ_E_CUDA;
+        return GJ_E_CUDA;
     }
+    if (cuda_device >= ndev) return GJ_E_INVALID;
     if (opt && opt->engine > GJ_ENGINE_FUSED) return GJ_E_INVALID;
     gj_ctx* ctx = new (std::nothrow) gj_ctx();
     if (!ctx) return GJ_E_NOMEM;

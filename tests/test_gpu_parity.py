@@ -139,6 +139,12 @@ def test_vertex_range_errors(ctx):
     assert ei.value.code == -2
 
 
+def test_create_rejects_device_past_the_last():
+    import ctypes
+    h = ctypes.c_void_p()
+    assert gj.lib().gj_create(1 << 20, None, ctypes.byref(h)) == -1 and not h.value
+
+
 def test_invalid_queries(ctx):
     for k, atoms, order in [(3, [(0, 0), (1, 2)], None), (3, [(0, 1)], None), (3, [(0, 1), (1, 2)], [0, 0, 1]),
                             (3, [(0, 1), (1, 2)], [0, 2, 1]), (4, [(0, 1), (2, 3)], None), (1, [(0, 0)], None)]:
