@@ -108,7 +108,11 @@ typedef struct {
  * (defaults). Errors: GJ_E_INVALID (negative or out-of-range device index,
  * bad engine), GJ_E_CUDA (no usable CUDA driver or device; a failed set-up). */
 int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out);
+/* Stops a request loop on ctx, waits for its stream and frees its memory
+ * and (if the context created it) its stream. ctx's graphs and queries must
+ * be freed first. NULL is ignored. */
 void gj_destroy(gj_ctx* ctx);
+/* A static English name of an error code ("unknown error" for others). */
 const char* gj_strerror(int code);
 /* Last error message recorded on ctx (empty string if none); valid until the next call. */
 const char* gj_last_error(const gj_ctx* ctx);
@@ -128,6 +132,8 @@ int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_
 int gj_graph_stats(const gj_graph* g, uint64_t* num_edges, uint64_t* version);
 /* Copies the forward index to host arrays: offsets [num_vertices + 1], neighbours [num_edges]. */
 int gj_graph_export(const gj_graph* g, int64_t* offsets, uint32_t* neighbours);
+/* Stops a request loop serving g, waits for the context's stream and frees
+ * g's device indices. NULL is ignored. */
 void gj_graph_free(gj_graph* g);
 
 /*
@@ -143,6 +149,8 @@ void gj_graph_free(gj_graph* g);
  */
 int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
                     gj_query** out);
+/* Frees q (host memory only). A query passed to a serving request must stay
+ * alive until that request is polled. NULL is ignored. */
 void gj_query_free(gj_query* q);
 
 /* Count and checksum of the matches of q in the committed graph, default engine.
@@ -209,8 +217,12 @@ typedef struct {
      * 2: off. Results never depend on it. */
     uint32_t donation;
 } gj_tuning;
+/* Copies the context's current settings to *out (fused_ms and plain_ms are
+ * 0: only gj_autotune's output carries them). Errors: GJ_E_INVALID (null pointer). */
 int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
-/* Errors: GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under 1 MiB, donation > 2). */
+/* Replaces the context's settings (fused_ms and plain_ms are ignored); results
+ * never depend on them. Errors: GJ_E_INVALID (seed_chunk out of range or not
+ * a multiple of 32, budget under 1 MiB, donation > 2). */
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
 /*
  * Chooses the context's launch settings by timing the given queries on the

@@ -225,17 +225,26 @@ int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_
     bool dev_s = is_device_ptr(src), dev_d = is_device_ptr(dst);
     if (m > 0 && (!dev_s || !dev_d)) {
         GJ_CUDA_TRY(ctx, cudaMallocAsync(&tmp, 2 * m * sizeof(uint32_t), st));
+        cudaError_t e = cudaSuccess;
         if (!dev_s) {
-            GJ_CUDA_TRY(ctx, cudaMemcpyAsync(tmp, src, m * 4, cudaMemcpyHostToDevice, st));
+            e = cudaMemcpyAsync(tmp, src, m * 4, cudaMemcpyHostToDevice, st);
             ds_ = tmp;
         }
-        if (!dev_d) {
-            GJ_CUDA_TRY(ctx, cudaMemcpyAsync(tmp + m, dst, m * 4, cudaMemcpyHostToDevice, st));
+        if (e == cudaSuccess && !dev_d) {
+            e = cudaMemcpyAsync(tmp + m, dst, m * 4, cudaMemcpyHostToDevice, st);
             dd_ = tmp + m;
+        }
+        if (e != cudaSuccess) {
+            cudaFreeAsync(tmp, st);
+            gj_set_error(ctx, GJ_E_CUDA, std::string("graph load: copy of the edge list: ") + cudaGetErrorString(e));
+            return GJ_E_CUDA;
         }
     }
     gj_graph* g = new (std::nothrow) gj_graph();
-    if (!g) return GJ_E_NOMEM;
+    if (!g) {
+        if (tmp) cudaFreeAsync(tmp, st);
+        return GJ_E_NOMEM;
+    }
     g->ctx = ctx;
     int rc = gj_csr_build(ctx, ds_, dd_, m, num_vertices, g);
     if (tmp) cudaFreeAsync(tmp, st);
