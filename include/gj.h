@@ -231,7 +231,9 @@ int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
  * for the fused engine, and a prefix-buffer budget in {64 MiB, 256 MiB,
  * 1 GiB, 2 GiB} up to prefix_cap_bytes (0 = 2 GiB) for the level-synchronous
  * engine (the memory/runtime trade-off of the paper's batch size). Applies
- * the fastest settings to g's context and returns them.
+ * the fastest settings to g's context and returns them. Errors:
+ * GJ_E_INVALID (null pointer, nq == 0, serving), and any error of the timed
+ * counts; on an error the context keeps its previous settings.
  */
 int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
                 uint32_t v_hi, gj_tuning* out);

@@ -84,6 +84,9 @@ bool is_device_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
+                   uint32_t v_hi, gj_tuning* out);
+
 struct DevSet {
     int prev = -1;
     explicit DevSet(int dev) {
@@ -385,6 +388,26 @@ int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t pr
     if (!g || !qs || !nq || !out) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
     if (ctx->server) return GJ_E_INVALID;
+    DevSet ds(ctx->device);
+    // on any failure the context keeps the settings it had before the call
+    const uint32_t old_chunk = ctx->seed_chunk, old_bps = ctx->blocks_per_sm;
+    const uint64_t old_bytes = ctx->opt.prefix_buffer_bytes;
+    const int rc = autotune_sweep(g, qs, nq, prefix_cap_bytes, v_lo, v_hi, out);
+    if (rc != GJ_OK) {
+        ctx->seed_chunk = old_chunk;
+        ctx->blocks_per_sm = old_bps;
+        ctx->opt.prefix_buffer_bytes = old_bytes;
+    }
+    return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
+                   uint32_t v_hi, gj_tuning* out) {
+    gj_ctx* ctx = g->ctx;
     std::vector<int64_t> c(nq);
     std::vector<uint64_t> h(nq);
     auto timed = [&](uint32_t engine, double* ms) -> int {
@@ -439,6 +462,10 @@ int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t pr
     out->plain_ms = best_bytes ? best_p : 0;
     return GJ_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int gj_last_work(const gj_ctx* ctx, gj_work_stats* out) {
     if (!ctx || !out) return GJ_E_INVALID;
