@@ -142,14 +142,29 @@ def lib():
     return _lib
 
 
-def _ptr(a):
-    """(pointer, keepalive) for a numpy array, a torch tensor (host or device) or None."""
+def _ptr(a, elem: int = 4):
+    """(pointer, keepalive) for a 1-D numpy array or sequence (converted to
+    uint32, or int8 when elem == 1), a 1-D contiguous torch tensor with
+    elem-byte elements (host or device), or None."""
     if a is None:
         return None, None
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if a.dim() != 1 or not a.is_contiguous() or a.element_size() != elem:
+            raise ValueError("tensor arguments must be 1-D, contiguous, with %d-byte elements" % elem)
         return ctypes.c_void_p(a.data_ptr()), a
-    arr = np.ascontiguousarray(a, dtype=np.uint32)
+    arr = np.ascontiguousarray(a, dtype=np.uint32 if elem == 4 else np.int8)
+    if arr.ndim != 1:
+        raise ValueError("array arguments must be 1-D")
     return ctypes.c_void_p(arr.ctypes.data), arr
+
+
+def _same_length(*arrays) -> int:
+    """The common length of the non-None arguments (0 if none); raises if they differ,
+    since the library reads that many entries of each."""
+    ns = {len(a) for a in arrays if a is not None}
+    if len(ns) > 1:
+        raise ValueError("edge arrays differ in length: %s" % sorted(ns))
+    return ns.pop() if ns else 0
 
 
 def _check(rc: int, ctx=None):
@@ -217,7 +232,7 @@ class Graph:
         self._h = None
         ps, ks = _ptr(src)
         pd, kd = _ptr(dst)
-        m = len(src) if src is not None else 0
+        m = _same_length(ks, kd)
         h = _VP()
         _check(lib().gj_graph_load(ctx._h, ps, pd, m, num_vertices, ctypes.byref(h)), ctx)
         self._h = h
@@ -336,12 +351,7 @@ def count_noalloc(g: Graph, qs):
 
 
 def _ptr8(a):
-    if a is None:
-        return None, None
-    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
-        return ctypes.c_void_p(a.data_ptr()), a
-    arr = np.ascontiguousarray(a, dtype=np.int8)
-    return ctypes.c_void_p(arr.ctypes.data), arr
+    return _ptr(a, 1)
 
 
 def apply_batch(g: Graph, src, dst, sign, qs=()):
@@ -349,7 +359,7 @@ def apply_batch(g: Graph, src, dst, sign, qs=()):
     ps, ks = _ptr(src)
     pd, kd = _ptr(dst)
     pg, kg = _ptr8(sign)
-    b = len(src)
+    b = _same_length(ks, kd, kg)
     n = len(qs)
     arr = (_VP * max(n, 1))(*[q._h for q in qs])
     c = np.zeros(max(n, 1), np.int64)
@@ -386,10 +396,11 @@ class Server:
         ps, ks = _ptr(src)
         pd, kd = _ptr(dst)
         pg, kg = _ptr8(sign)
+        b = _same_length(ks, kd, kg)
         n = len(qs)
         arr = (_VP * max(n, 1))(*[q._h for q in qs])
         rid = ctypes.c_uint64(0)
-        _check(lib().gj_submit_batch(self.ctx._h, ps, pd, pg, len(src), arr if n else None, n, ctypes.byref(rid)),
+        _check(lib().gj_submit_batch(self.ctx._h, ps, pd, pg, b, arr if n else None, n, ctypes.byref(rid)),
                self.ctx)
         self._keep[rid.value] = list(qs)
         return rid.value

@@ -39,3 +39,29 @@ def test_null_arguments_are_rejected_without_device_work():
 def test_create_rejects_negative_device():
     h = ctypes.c_void_p()
     assert gj.lib().gj_create(-1, None, ctypes.byref(h)) == -1
+
+
+def test_marshalling_rejects_arrays_the_library_would_misread():
+    """The library reads len(src) entries of every edge array: unequal lengths,
+    2-D arrays and tensors with the wrong element size or layout are refused
+    before any call (on a device pointer an overlong read could fault)."""
+    import numpy as np
+    import pytest
+    import torch
+
+    with pytest.raises(ValueError):
+        gj._same_length(np.zeros(3, np.uint32), np.zeros(4, np.uint32))
+    assert gj._same_length(np.zeros(5, np.uint32), None, np.zeros(5, np.int8)) == 5
+    assert gj._same_length(None, None) == 0
+    with pytest.raises(ValueError):
+        gj._ptr(np.zeros((2, 2), np.uint32))
+    t = torch.arange(10, dtype=torch.int32)
+    p, keep = gj._ptr(t)
+    assert p.value == t.data_ptr() and keep is t
+    for bad in (t[::2], torch.arange(10, dtype=torch.int64), t.reshape(2, 5)):
+        with pytest.raises(ValueError):
+            gj._ptr(bad)
+    with pytest.raises(ValueError):
+        gj._ptr8(t)
+    p8, keep8 = gj._ptr8([1, -1, 1])
+    assert keep8.dtype == np.int8 and keep8.tolist() == [1, -1, 1]
