@@ -5,8 +5,11 @@ Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 
 ``gj_oracle.c`` is a plain single-threaded C implementation of Generic Join
 (Fig. 1, Section 2.2) starting from P0 = {()}, and of Delta-GJ's delta
-queries (Section 3.3.1). It shares no code with the CUDA path. This module
-only marshals arguments through ctypes and compiles the C file with gcc.
+queries (Section 3.3.1), with the specialisations of Section 5.4
+(inequality constraints, degree-ordered renaming, the ternary triangle
+relation, factorised output). It shares no code with the CUDA path. This
+module only marshals arguments through ctypes and compiles the C file with
+gcc.
 
 Pins (what fixes the oracle other than itself) live in tests/test_oracle.py:
 brute-force enumeration of V^k on tiny graphs, closed forms on complete
@@ -85,6 +88,14 @@ def _load():
             lib.og_count.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint32, u32p, ctypes.c_uint32,
                                      ctypes.c_uint32, ctypes.c_int, i64p, u64p, ctypes.POINTER(Stats), u32p,
                                      ctypes.c_uint64, u64p]
+            lib.og_count_ex.restype = ctypes.c_int
+            lib.og_count_ex.argtypes = [vp, ctypes.c_uint32, u32p, ctypes.c_uint32, u32p, ctypes.c_uint32, u32p,
+                                        ctypes.c_uint32, u32p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, i64p,
+                                        u64p, ctypes.POINTER(Stats), u32p, ctypes.c_uint64, u64p]
+            lib.og_graph_num_triangles.restype = ctypes.c_uint64
+            lib.og_graph_num_triangles.argtypes = [vp]
+            lib.og_graph_transform.restype = vp
+            lib.og_graph_transform.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, ip]
             lib.og_normalize.restype = ctypes.c_int64
             lib.og_normalize.argtypes = [vp, u32p, u32p, i8p, ctypes.c_uint64, u32p, u32p, i8p]
             lib.og_graph_apply.restype = vp
@@ -122,22 +133,37 @@ def tuple_hash(xs) -> int:
 
 
 class Query:
-    """Q(a_0..a_{k-1}) := E(a_s, a_d), ...; atoms as (s, d) pairs of attribute ids."""
+    """Q(a_0..a_{k-1}) := E(a_s, a_d), ..., tri(a_i, a_j, a_l), ... with x_a < x_b constraints.
 
-    def __init__(self, k: int, atoms, order=None):
+    atoms: (s, d) pairs of attribute ids (edge atoms); tri: (i, j, l) triples
+    (the ternary triangle relation of Section 5.4: i -> j, i -> l, j -> l,
+    indexed by (i, j)); lt: (a, b) pairs meaning x_a < x_b (Section 5.4's
+    inequality constraints, on vertex ids)."""
+
+    def __init__(self, k: int, atoms, order=None, tri=(), lt=()):
         self.k = k
         self.atoms = [tuple(a) for a in atoms]
+        self.tri = [tuple(t) for t in tri]
+        self.lt = [tuple(c) for c in lt]
         self.order = list(order) if order is not None else None
-        self._atoms = np.array([x for a in self.atoms for x in a], dtype=np.uint32)
+        self._atoms = np.array([x for a in self.atoms for x in a] or [0], dtype=np.uint32)
+        self._tri = np.array([x for t in self.tri for x in t] or [0], dtype=np.uint32)
+        self._lt = np.array([x for c in self.lt for x in c] or [0], dtype=np.uint32)
         self._order = np.array(self.order, dtype=np.uint32) if self.order is not None else None
 
     def with_order(self, order):
-        return Query(self.k, self.atoms, order)
+        return Query(self.k, self.atoms, order, self.tri, self.lt)
 
     def _args(self):
-        pa = self._atoms.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+        pa = self._atoms.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if self.atoms else None
         po = self._order.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)) if self._order is not None else None
         return pa, len(self.atoms), po
+
+    def _ext_args(self):
+        p = ctypes.POINTER(ctypes.c_uint32)
+        pt = self._tri.ctypes.data_as(p) if self.tri else None
+        pl = self._lt.ctypes.data_as(p) if self.lt else None
+        return pt, len(self.tri), pl, len(self.lt)
 
 
 class Graph:
@@ -182,17 +208,36 @@ class Graph:
 
         mode 0: Generic Join from P0 as in Fig. 1 (the definition); mode 1:
         the paper's implementation (edge seeds, bound atoms only, Section 4.1
-        and Section 4.2), whose work units the CUDA path reports."""
+        and Section 4.2), whose work units the CUDA path reports; mode 2:
+        mode 1 with factorised output for trailing attributes that constrain
+        one another in no way (Section 5.4)."""
         lo, hi = first_range if first_range is not None else (0, 0xFFFFFFFF)
         c = ctypes.c_int64(0)
         h = ctypes.c_uint64(0)
         st = Stats() if stats else None
         pa, na, po = q._args()
-        _check(_load().og_count(self._h, q.k, pa, na, po, lo, hi, mode, ctypes.byref(c), ctypes.byref(h),
-                                ctypes.byref(st) if st is not None else None, None, 0, None))
+        pt, nt, pl, nl = q._ext_args()
+        _check(_load().og_count_ex(self._h, q.k, pa, na, pt, nt, pl, nl, po, lo, hi, mode, ctypes.byref(c),
+                                   ctypes.byref(h), ctypes.byref(st) if st is not None else None, None, 0, None))
         if stats:
             return c.value, h.value, st
         return c.value, h.value
+
+    def num_triangles(self) -> int:
+        """Tuples of the ternary relation tri (a -> b, a -> c, b -> c)."""
+        return int(_load().og_graph_num_triangles(self._h))
+
+    def transform(self, symmetrize: bool = False, degree_order: bool = False, orient: bool = False):
+        """(graph, new_of_old) after symmetry breaking's input transformation (Section 5.4):
+        optional symmetrisation, renaming by ascending degree (ties by id), and keeping
+        only the edges from a lower to a higher new id."""
+        m = np.empty(max(self.n, 1), np.uint32)
+        err = ctypes.c_int(0)
+        h = _load().og_graph_transform(self._h, int(symmetrize), int(degree_order), int(orient),
+                                       m.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), ctypes.byref(err))
+        if not h:
+            _check(err.value or -3)
+        return Graph(self.n, None, None, _handle=h), m[:self.n].copy()
 
     def list(self, q: Query, cap: int | None = None):
         """All matches as a (count, k) uint32 array in query attribute order, plus the checksum."""
@@ -203,8 +248,10 @@ class Graph:
         h = ctypes.c_uint64(0)
         w = ctypes.c_uint64(0)
         pa, na, po = q._args()
-        _check(_load().og_count(self._h, q.k, pa, na, po, 0, 0xFFFFFFFF, 0, ctypes.byref(c), ctypes.byref(h), None,
-                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap, ctypes.byref(w)))
+        pt, nt, pl, nl = q._ext_args()
+        _check(_load().og_count_ex(self._h, q.k, pa, na, pt, nt, pl, nl, po, 0, 0xFFFFFFFF, 1 if q.tri else 0,
+                                   ctypes.byref(c), ctypes.byref(h), None,
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap, ctypes.byref(w)))
         return out[:w.value], h.value
 
     def normalize(self, src, dst, sign):

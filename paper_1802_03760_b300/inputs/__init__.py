@@ -200,7 +200,9 @@ class UpdateStream:
 # transitive triangles sharing the atom E(a2,a3). "4-cycle" is the paper's
 # four-atom shape e(a1,a2), e(a2,a3), e(a4,a1), e(a4,a3). "triangle" is the
 # transitive triangle of Section 5.1; "cyclic-triangle" is the one of
-# Section 1 and Appendix A.
+# Section 1 and Appendix A. "house" is the query of Section 5.4: a2..a5 form
+# a clique and a1 is joined to a2 and a3 only (every edge oriented from the
+# lower to the higher attribute).
 QUERIES = {
     "triangle": (3, [(0, 1), (1, 2), (0, 2)]),
     "cyclic-triangle": (3, [(0, 1), (1, 2), (2, 0)]),
@@ -208,6 +210,33 @@ QUERIES = {
     "diamond": (4, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2)]),
     "4-clique": (4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]),
     "5-clique": (5, [(i, j) for i in range(5) for j in range(i + 1, 5)]),
+    "house": (5, [(0, 1), (0, 2), (1, 2), (1, 3), (1, 4), (2, 3), (2, 4), (3, 4)]),
+}
+
+# Formulations of the shapes above with the specialisations of Section 5.4,
+# as keyword arguments of a query definition: "tri" lists ternary atoms
+# tri(a_i, a_j, a_l) over the graph's triangles (a_i -> a_j, a_i -> a_l,
+# a_j -> a_l, indexed by (a_i, a_j)); "lt" lists inequalities x_a < x_b
+# (symmetry breaking on a symmetrised graph); "order" is an attribute
+# order whose trailing attributes constrain one another in no way, so that
+# their extensions can be factorised. Each has the same matches as the
+# shape it is named after (on the graphs stated).
+SPECIALISED = {
+    # triangle indexing: each 4-clique is three triangles on a1
+    "4-clique-tr": dict(k=4, atoms=[], tri=[(0, 1, 2), (0, 1, 3), (0, 2, 3)], lt=[], order=None),
+    "5-clique-tr": dict(k=5, atoms=[], tri=[(0, 1, 2), (0, 1, 3), (0, 2, 3), (0, 1, 4), (0, 2, 4), (0, 3, 4)],
+                        lt=[], order=None),
+    # factorised: a1 and a4 (diamond), a1 and a5 (house) extend independently
+    "diamond-f": dict(k=4, atoms=QUERIES["diamond"][1], tri=[], lt=[], order=[1, 2, 0, 3]),
+    "house-f": dict(k=5, atoms=QUERIES["house"][1], tri=[], lt=[], order=[1, 2, 3, 0, 4]),
+    # house with its clique a2..a5 from triangles and a1 joined by edge atoms, factorised
+    "house-tr": dict(k=5, atoms=[(0, 1), (0, 2)], tri=[(1, 2, 3), (1, 2, 4), (1, 3, 4), (2, 3, 4)], lt=[],
+                     order=[1, 2, 3, 0, 4]),
+    # symmetry breaking on a symmetrised graph: one match per undirected subgraph
+    "4-clique-sym": dict(k=4, atoms=QUERIES["4-clique"][1], tri=[], lt=[(0, 1), (1, 2), (2, 3)], order=None),
+    "5-clique-sym": dict(k=5, atoms=QUERIES["5-clique"][1], tri=[], lt=[(0, 1), (1, 2), (2, 3), (3, 4)],
+                         order=None),
+    "house-sym": dict(k=5, atoms=QUERIES["house"][1], tri=[], lt=[(1, 2), (3, 4)], order=[1, 2, 3, 0, 4]),
 }
 
 
