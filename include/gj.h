@@ -128,6 +128,37 @@ const char* gj_last_error(const gj_ctx* ctx);
  */
 int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
                   gj_graph** out);
+/* Flags of gj_graph_load_ex: the input transformation of symmetry breaking
+ * (Section 5.4). GJ_LOAD_SYMMETRIZE adds the reverse of every edge (the
+ * undirected graph). GJ_LOAD_DEGREE_ORDER gives the vertices new ids that
+ * ascend with their out-degree (after the optional symmetrisation; ties
+ * keep the order of the old ids); the indices, queries and results then
+ * use the new ids (gj_graph_relabel_map gives them). GJ_LOAD_ORIENT keeps
+ * only the edges from a lower to a higher (new) id, so that a clique query
+ * with atoms E(a_i, a_j), i < j, finds each undirected clique once. */
+enum { GJ_LOAD_SYMMETRIZE = 1, GJ_LOAD_DEGREE_ORDER = 2, GJ_LOAD_ORIENT = 4 };
+/* gj_graph_load with the GJ_LOAD_* flags above (0: gj_graph_load). Host
+ * or device arrays; device arrays must be on the context's device and
+ * complete (written by work that has finished, or is ordered before the
+ * context's stream). Errors: as gj_graph_load, and GJ_E_INVALID (unknown
+ * flag, an array in another device's memory). */
+int gj_graph_load_ex(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
+                     uint32_t flags, gj_graph** out);
+/* new_of_old[v] = the id that input vertex v has in g's indices (v itself
+ * unless g was loaded with GJ_LOAD_DEGREE_ORDER); host array of
+ * num_vertices. Errors: GJ_E_INVALID, GJ_E_CUDA. */
+int gj_graph_relabel_map(const gj_graph* g, uint32_t* new_of_old);
+/*
+ * Builds g's triangle index, the ternary relation tri(a, b, c) of triangle
+ * indexing (Section 5.4): the tuples with a -> b, a -> c and b -> c, indexed
+ * by (a, b), i.e. for every edge a -> b the sorted list of the c that
+ * complete a triangle on it. Queries with tri atoms read it; counting such
+ * a query builds it when it is missing, and applying an update batch drops
+ * it (it describes one version of the graph). *count (may be NULL) receives
+ * the number of tuples. Errors: GJ_E_INVALID (null g, serving), GJ_E_NOMEM,
+ * GJ_E_CUDA.
+ */
+int gj_graph_build_triangles(gj_graph* g, uint64_t* count);
 /* Number of distinct edges and the committed version (0 after load, +1 per applied batch). */
 int gj_graph_stats(const gj_graph* g, uint64_t* num_edges, uint64_t* version);
 /* Copies the forward index to host arrays: offsets [num_vertices + 1], neighbours [num_edges]. */
@@ -149,6 +180,27 @@ void gj_graph_free(gj_graph* g);
  */
 int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
                     gj_query** out);
+/*
+ * gj_query_define with the specialisations of Section 5.4. tri_atoms holds
+ * n_tri triples (i, j, l): the atom tri(a_i, a_j, a_l) holds when a_i ->
+ * a_j, a_i -> a_l and a_j -> a_l are edges (the triangle index, indexed by
+ * (a_i, a_j)); a_l must come after a_i and a_j in the order, and a tri atom
+ * whose first two attributes are the first two of the order can seed the
+ * evaluation (every edge between them is a seed). lt_pairs holds n_lt pairs
+ * (a, b): matches must have x_a < x_b (vertex ids; symmetry breaking).
+ * atoms may be NULL when n_atoms is 0. Queries with tri atoms cannot be
+ * used in update batches or serving requests (GJ_E_INVALID there). When the
+ * last attributes of the order do not depend on every earlier one (for
+ * example the diamond in order a2, a3, a1, a4, or the house query of
+ * Section 5.4), the fused engine extends prefixes that agree on what the
+ * last level reads once for all of them (aggregation of identical lookups,
+ * Section 3.4.2) and hashes the matches of each. Errors: as
+ * gj_query_define, and a tri atom or inequality with equal or out-of-range
+ * attributes, or a tri atom whose third attribute comes too early.
+ */
+int gj_query_define_ex(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* tri_atoms,
+                       uint32_t n_tri, const uint32_t* lt_pairs, uint32_t n_lt, const uint32_t* order,
+                       gj_query** out);
 /* Frees q (host memory only). A query passed to a serving request must stay
  * alive until that request is polled. NULL is ignored. */
 void gj_query_free(gj_query* q);

@@ -74,14 +74,23 @@ int gj_timer_collect(gj_ctx* ctx) {
 
 namespace {
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// 1: device memory of device dev, 0: host memory, -1: another device's memory
+int ptr_kind(const void* p, int dev) {
+    if (!p) return 0;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return 0;
+    return at.device == dev ? 1 : -1;
+}
+
+// Queries with tri atoms read the graph's triangle index: build it if missing.
+int ensure_tri(gj_ctx* ctx, gj_graph* g, const gj_query* const* qs, uint32_t nq) {
+    for (uint32_t i = 0; i < nq; i++)
+        if (qs[i]->ntri) return gj_tri_build(ctx, g);
+    return GJ_OK;
 }
 
 int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t prefix_cap_bytes, uint32_t v_lo,
@@ -204,38 +213,44 @@ void gj_graph_free(gj_graph* g) {
     if (g->ctx->server) gj_serve_stop(g->ctx);  // the loop may still read g
     DevSet ds(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
-    for (gj_csr* c : {&g->fwd, &g->rev}) {
-        if (c->off) cudaFree(c->off);
-        if (c->nbr) cudaFree(c->nbr);
-        if (c->key) cudaFree(c->key);
-        if (c->tab_off) cudaFree(c->tab_off);
-        if (c->tab) cudaFree(c->tab);
-    }
+    for (gj_csr* c : {&g->fwd, &g->rev}) gj_csr_release(*c);
+    gj_tri_release(g->tri);
+    if (g->relabel) cudaFree(g->relabel);
     delete g;
 }
 
-int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
-                  gj_graph** out) {
+int gj_graph_load_ex(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
+                     uint32_t flags, gj_graph** out) {
     if (!ctx || !out || num_vertices == 0 || num_vertices == UINT32_MAX || (m > 0 && (!src || !dst)))
         return GJ_E_INVALID;
+    if (flags & ~(uint32_t)(GJ_LOAD_SYMMETRIZE | GJ_LOAD_DEGREE_ORDER | GJ_LOAD_ORIENT)) return GJ_E_INVALID;
     *out = nullptr;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     cudaStream_t st = ctx->stream;
+    const int ks = ptr_kind(src, ctx->device), kd = ptr_kind(dst, ctx->device);
+    if (m > 0 && (ks < 0 || kd < 0)) {
+        gj_set_error(ctx, GJ_E_INVALID, "graph load: an edge array is in another device's memory");
+        return GJ_E_INVALID;
+    }
+    const bool sym = flags & GJ_LOAD_SYMMETRIZE;
+    const uint64_t mm = sym ? 2 * m : m;  // with symmetrisation: (src, dst) then (dst, src)
     const uint32_t* ds_ = src;
     const uint32_t* dd_ = dst;
     uint32_t* tmp = nullptr;
-    bool dev_s = is_device_ptr(src), dev_d = is_device_ptr(dst);
-    if (m > 0 && (!dev_s || !dev_d)) {
-        GJ_CUDA_TRY(ctx, cudaMallocAsync(&tmp, 2 * m * sizeof(uint32_t), st));
+    if (m > 0 && (sym || ks == 0 || kd == 0)) {
+        GJ_CUDA_TRY(ctx, cudaMallocAsync(&tmp, 2 * mm * sizeof(uint32_t), st));
         cudaError_t e = cudaSuccess;
-        if (!dev_s) {
-            e = cudaMemcpyAsync(tmp, src, m * 4, cudaMemcpyHostToDevice, st);
-            ds_ = tmp;
-        }
-        if (e == cudaSuccess && !dev_d) {
-            e = cudaMemcpyAsync(tmp + m, dst, m * 4, cudaMemcpyHostToDevice, st);
-            dd_ = tmp + m;
+        ds_ = tmp;
+        dd_ = tmp + mm;
+        for (int half = 0; half < (sym ? 2 : 1) && e == cudaSuccess; half++) {
+            const uint32_t* a = half ? dst : src;  // sources of this half
+            const uint32_t* b = half ? src : dst;
+            const int ka = half ? kd : ks, kb = half ? ks : kd;
+            e = cudaMemcpyAsync(tmp + half * m, a, m * 4, ka ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tmp + mm + half * m, b, m * 4,
+                                    kb ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
         }
         if (e != cudaSuccess) {
             cudaFreeAsync(tmp, st);
@@ -249,13 +264,44 @@ int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_
         return GJ_E_NOMEM;
     }
     g->ctx = ctx;
-    int rc = gj_csr_build(ctx, ds_, dd_, m, num_vertices, g);
+    g->load_flags = flags;
+    int rc = gj_csr_build(ctx, ds_, dd_, mm, num_vertices, g);
     if (tmp) cudaFreeAsync(tmp, st);
+    if (rc == GJ_OK) rc = gj_graph_transform(ctx, g, flags);
     if (rc != GJ_OK) {
         gj_graph_free(g);
         return rc;
     }
     *out = g;
+    return GJ_OK;
+}
+
+int gj_graph_load(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint64_t m, uint32_t num_vertices,
+                  gj_graph** out) {
+    return gj_graph_load_ex(ctx, src, dst, m, num_vertices, 0, out);
+}
+
+int gj_graph_relabel_map(const gj_graph* g, uint32_t* new_of_old) {
+    if (!g || !new_of_old) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    if (!g->relabel) {
+        for (uint32_t v = 0; v < g->n; v++) new_of_old[v] = v;
+        return GJ_OK;
+    }
+    DevSet ds(ctx->device);
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    GJ_CUDA_TRY(ctx, cudaMemcpy(new_of_old, g->relabel, sizeof(uint32_t) * g->n, cudaMemcpyDeviceToHost));
+    return GJ_OK;
+}
+
+int gj_graph_build_triangles(gj_graph* g, uint64_t* count) {
+    if (!g) return GJ_E_INVALID;
+    gj_ctx* ctx = g->ctx;
+    if (ctx->server) return GJ_E_INVALID;
+    DevSet ds(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_TRY(gj_tri_build(ctx, g));
+    if (count) *count = g->tri.count;
     return GJ_OK;
 }
 
@@ -276,12 +322,13 @@ int gj_graph_export(const gj_graph* g, int64_t* offsets, uint32_t* neighbours) {
     return GJ_OK;
 }
 
-int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
-                    gj_query** out) {
-    if (!ctx || !atoms || !out) return GJ_E_INVALID;
+int gj_query_define_ex(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* tri_atoms,
+                       uint32_t n_tri, const uint32_t* lt_pairs, uint32_t n_lt, const uint32_t* order,
+                       gj_query** out) {
+    if (!ctx || !out || (n_atoms && !atoms) || (n_tri && !tri_atoms) || (n_lt && !lt_pairs)) return GJ_E_INVALID;
     *out = nullptr;
-    if (n_atoms > GJ_MAX_ATOMS || k > GJ_MAX_K) {
-        gj_set_error(ctx, GJ_E_INVALID, "k > 8 or n_atoms > 16");
+    if (n_atoms > GJ_MAX_ATOMS || n_tri > GJ_MAX_ATOMS || n_lt > GJ_MAX_ATOMS || k > GJ_MAX_K || k < 2) {
+        gj_set_error(ctx, GJ_E_INVALID, "k must be in [2, 8] and each list hold at most 16 entries");
         return GJ_E_INVALID;
     }
     gj_query* q = new (std::nothrow) gj_query();
@@ -289,19 +336,30 @@ int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_a
     q->ctx = ctx;
     q->k = k;
     q->natoms = n_atoms;
+    q->ntri = n_tri;
+    q->nlt = n_lt;
     for (uint32_t t = 0; t < n_atoms; t++) {
         q->as[t] = atoms[2 * t];
         q->ad[t] = atoms[2 * t + 1];
     }
+    for (uint32_t t = 0; t < n_tri; t++) {
+        q->ta[t] = tri_atoms[3 * t];
+        q->tb[t] = tri_atoms[3 * t + 1];
+        q->tc[t] = tri_atoms[3 * t + 2];
+    }
+    for (uint32_t t = 0; t < n_lt; t++) {
+        q->la[t] = lt_pairs[2 * t];
+        q->lb[t] = lt_pairs[2 * t + 1];
+    }
+    for (uint32_t j = 0; j < k; j++) q->order[j] = order ? order[j] : j;
     std::string why;
-    int rc = gj_plan_compile(q->as, q->ad, n_atoms, k, order, &q->plan, &why);
+    int rc = gj_plan_compile(q, &q->plan, &why);
     if (rc != GJ_OK) {
         gj_set_error(ctx, rc, "query: " + why);
         delete q;
         return rc;
     }
-    for (uint32_t j = 0; j < k; j++) q->order[j] = q->plan.order[j];
-    for (uint32_t i = 0; i < n_atoms; i++) {
+    for (uint32_t i = 0; i < n_atoms && n_tri == 0; i++) {
         rc = gj_plan_compile_delta(q, i, &q->dplan[i], &why);
         if (rc != GJ_OK) {
             gj_set_error(ctx, rc, "query: " + why);
@@ -313,6 +371,12 @@ int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_a
     return GJ_OK;
 }
 
+int gj_query_define(gj_ctx* ctx, uint32_t k, const uint32_t* atoms, uint32_t n_atoms, const uint32_t* order,
+                    gj_query** out) {
+    if (!atoms) return GJ_E_INVALID;
+    return gj_query_define_ex(ctx, k, atoms, n_atoms, nullptr, 0, nullptr, 0, order, out);
+}
+
 void gj_query_free(gj_query* q) { delete q; }
 
 int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, uint32_t v_hi, int64_t* count,
@@ -322,6 +386,7 @@ int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, 
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_TRY(ensure_tri(ctx, g, &q, 1));
     int rc;
     if (engine == GJ_ENGINE_PLAIN)
         rc = gj_engine_plain(ctx, g, q, v_lo, v_hi, count, checksum, nullptr, 0, nullptr);
@@ -340,6 +405,7 @@ int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_TRY(ensure_tri(ctx, g, qs, nq));
     if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, v_lo, v_hi, counts, checksums);
     gj_work_stats sum{};
     for (uint32_t i = 0; i < nq; i++) {
@@ -486,13 +552,21 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
         if (!qs[i] || qs[i]->ctx != g->ctx) return GJ_E_INVALID;
     gj_ctx* ctx = g->ctx;
     if (ctx->server) return GJ_E_INVALID;
+    for (uint32_t i = 0; i < nq; i++)
+        if (qs[i]->ntri) {
+            gj_set_error(ctx, GJ_E_INVALID, "update batch: queries with tri atoms have no delta queries");
+            return GJ_E_INVALID;
+        }
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
     DeltaBuf buf;
+    // the deltas go to the caller's arrays only once the batch is committed
+    std::vector<int64_t> dc(nq);
+    std::vector<uint64_t> dh(nq);
     int rc = gj_delta_prepare(ctx, g, src, dst, sign, b, &buf);
     if (rc == GJ_OK) rc = gj_delta_eval(ctx, g, buf.batch, qs, nq,
                                          (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN,
-                                         delta_count, delta_checksum);
+                                         dc.data(), dh.data());
     gj_work_stats sum = ctx->work;
     const uint64_t changes = buf.batch.n;
     if (rc == GJ_OK) rc = gj_delta_commit(ctx, g, buf.batch);
@@ -501,6 +575,10 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
         GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         g->last_changes = changes;
         ctx->work = sum;
+        for (uint32_t i = 0; i < nq; i++) {
+            delta_count[i] = dc[i];
+            delta_checksum[i] = dh[i];
+        }
     }
     return rc;
 }
@@ -571,6 +649,7 @@ int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, 
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_TRY(ensure_tri(ctx, g, &q, 1));
     int64_t c = 0;
     uint64_t h = 0;
     GJ_TRY(gj_engine_plain(ctx, g, q, 0, UINT32_MAX, &c, &h, out_tuples, cap, written));

@@ -184,14 +184,16 @@ __global__ void k_merge_slots(const uint32_t* __restrict__ ak, const uint32_t* _
     }
 }
 
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
+// 1: device memory of device dev, 0: host memory, -1: another device's memory
+int ptr_kind(const void* p, int dev) {
+    if (!p) return 0;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return 0;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return 0;
+    return at.device == dev ? 1 : -1;
 }
 
 struct Arena {
@@ -241,22 +243,27 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
     while ((1ull << mbits) < 2 * bb) mbits++;
     const size_t map_bytes = 2 * ((size_t)4 << mbits) + 2 * ((size_t)16 << mbits);
     const size_t bytes = 120 * bb + map_bytes + 72 * 256;
+    const int k_src = ptr_kind(src, ctx->device), k_dst = ptr_kind(dst, ctx->device), k_sign = ptr_kind(sign, ctx->device);
+    if (b && (k_src < 0 || k_dst < 0 || k_sign < 0)) {
+        gj_set_error(ctx, GJ_E_INVALID, "update batch: an input array is in another device's memory");
+        return GJ_E_INVALID;
+    }
     GJ_CUDA_TRY(ctx, cudaMallocAsync(&out->mem, bytes, st));
     Arena A{(char*)out->mem, 0, bytes};
     const uint32_t* d_src = src;
     const uint32_t* d_dst = dst;
     const int8_t* d_sign = sign;
-    if (b && !is_device_ptr(src)) {
+    if (b && k_src == 0) {
         uint32_t* t = (uint32_t*)A.take(4 * bb);
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(t, src, 4 * b, cudaMemcpyHostToDevice, st));
         d_src = t;
     }
-    if (b && !is_device_ptr(dst)) {
+    if (b && k_dst == 0) {
         uint32_t* t = (uint32_t*)A.take(4 * bb);
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(t, dst, 4 * b, cudaMemcpyHostToDevice, st));
         d_dst = t;
     }
-    if (b && !is_device_ptr(sign)) {
+    if (b && k_sign == 0) {
         int8_t* t = (int8_t*)A.take(bb);
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(t, sign, b, cudaMemcpyHostToDevice, st));
         d_sign = t;
@@ -446,5 +453,6 @@ int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_f
     g->rev = nr;
     g->m = mf;
     g->version++;
+    gj_tri_release(g->tri);  // the triangle index described the previous version
     return GJ_OK;
 }

@@ -79,22 +79,28 @@ struct FusedArgs {
 constexpr uint32_t IDLE_WAIT_LIMIT = 1u << 26;  // iterations of the idle wait before giving up
 
 // Shared-memory layout of one warp (identical on host and device): the
-// plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), then
-// per level j >= 2 the prefix tuples [j][FC] (column-major), the min-list
-// pointers [FC], the candidate offsets [FC + 1], the hash prefixes [FC] and
-// the min-i bytes [FC]. Offsets are closed forms so that no per-level table
-// sits in local memory.
+// plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), the
+// buffer of matches waiting to be hashed for an aggregated group, then per
+// level j >= 2 the prefix tuples [j][FC] (column-major), the min-list
+// pointers [FC], the candidate offsets [FC + 1], the hash prefixes [FC], the
+// min-i bytes [FC] and the group sizes [FC]. Offsets are closed forms so
+// that no per-level table sits in local memory.
 constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
-constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC;  // mptr + cs + hpre + minb
+// Matches of an aggregated last-level group wait here until 64 or more can
+// be hashed against every member of the group at once.
+constexpr uint32_t SV_CAP = 128;
+constexpr uint32_t SV_BYTES = SV_CAP * 4;
+constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC + FC;  // mptr + cs + hpre + minb + grp
 // Delta plans also keep, per prefix, the new-version parts of the min list
 // (inserts, deletes, committed length) and the seed's sign.
 constexpr uint32_t LVL_DELTA = FC * 8 + FC * 8 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
 __host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d) { return LVL_FIXED + (d ? ALIGN16(LVL_DELTA) : 0); }
 __host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d = false) {
     // sum over i = 2..j-1 of (FC * i * 4 + fixed part)
-    return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + lvl_size_fixed(d) * (j - 2);
+    return PLAN_BYTES + SCAL_BYTES + SV_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) +
+           lvl_size_fixed(d) * (j - 2);
 }
 __host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d = false) { return lvl_base(j, d); }
 __host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d = false) { return lvl_base(j, d) + FC * 4 * j; }
@@ -103,13 +109,15 @@ __host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j, bool d = false
     return off_cs(j, d) + ALIGN16((FC + 1) * 8);
 }
 __host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d = false) { return off_hpre(j, d) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j) { return off_minb(j, true) + FC; }
+// group size of an aggregated last-level prefix (leaders only)
+__host__ __device__ __forceinline__ uint32_t off_grp(uint32_t j, bool d = false) { return off_minb(j, d) + FC; }
+__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j) { return off_grp(j, true) + FC; }
 __host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j) { return off_dins(j) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j) { return off_ddel(j) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j) { return off_dblen(j) + FC * 4; }
 __host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j) { return off_dndel(j) + FC * 4; }
 __host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d = false) {
-    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : lvl_base(kmax, d);
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES + SV_BYTES : lvl_base(kmax, d);
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
@@ -204,6 +212,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     uint64_t* cur_ = n_ + GJ_MAX_K;
     uint64_t* tot_ = cur_ + GJ_MAX_K;
     uint64_t* ip_ = tot_ + GJ_MAX_K;  // prefix that owns candidate cur_ (advances monotonically)
+    uint32_t* sv = reinterpret_cast<uint32_t*>(ws + PLAN_BYTES + SCAL_BYTES);  // [SV_CAP]
     const GraphView& G = A.G;
     const uint64_t space = A.qbase[A.nq];
 
@@ -240,11 +249,24 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         uint8_t* minb = ws + off_minb(j, DELTA);
         const bool last = (j == (int)k - 1);
         const uint32_t a_new = P.order[j];
+        // aggregation: a prefix that agrees with the one before it on every
+        // position the last level reads has the same extensions; it joins
+        // that prefix's group and proposes nothing itself
+        const uint32_t aggm = (!DELTA && last) ? P.agg : 0u;
         uint64_t len2[2];
+        uint64_t all2 = 0;  // the min counts of every prefix, members of groups included
+        bool lead2[2];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             uint32_t i = lane + 32 * h;
             uint64_t best = 0;
+            bool lead = i < nj;
+            if (aggm && i > 0 && i < nj) {
+                lead = false;
+                for (uint32_t p = 0; p < (uint32_t)j; p++)
+                    if (((aggm >> p) & 1u) && tup[p * FC + i] != tup[p * FC + i - 1]) lead = true;
+            }
+            lead2[h] = lead;
             if (i < nj) {
                 best = ~0ull;
                 uint32_t bi = 0;
@@ -272,15 +294,27 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 } else {
                     for (uint32_t b = 0; b < P.nb[j]; b++) {
                         uint32_t v = tup[P.bpos[j][b] * FC + i];
-                        const int64_t* off = P.bdir[j][b] ? G.ro : G.fo;
-                        int64_t s = __ldg(off + v);
-                        uint64_t len = (uint64_t)(__ldg(off + v + 1) - s);
+                        const uint32_t dir = P.bdir[j][b];
+                        uint64_t len;
+                        const uint32_t* lp;
+                        if (dir == GJ_BIND_TRI) {
+                            const BindList L = gj_bind_list(G, dir, v, tup[P.bpos2[j][b] * FC + i]);
+                            len = L.len;
+                            lp = L.p;
+                        } else {
+                            const int64_t* off = dir ? G.ro : G.fo;
+                            int64_t s = __ldg(off + v);
+                            len = (uint64_t)(__ldg(off + v + 1) - s);
+                            lp = (dir ? G.rn : G.fn) + s;
+                        }
                         if (len < best) {
                             best = len;
                             bi = b;
-                            bp = (P.bdir[j][b] ? G.rn : G.fn) + s;
+                            bp = lp;
                         }
                     }
+                    all2 += best;
+                    if (!lead) best = 0;
                 }
                 mptr[i] = bp;
                 minb[i] = (uint8_t)bi;
@@ -291,6 +325,22 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
             }
             len2[h] = best;
+        }
+        if (aggm)
+            for (int o = 16; o > 0; o >>= 1) all2 += __shfl_xor_sync(0xffffffffu, all2, o);
+        if (aggm) {
+            const uint32_t l0 = __ballot_sync(0xffffffffu, lead2[0]), l1 = __ballot_sync(0xffffffffu, lead2[1]);
+            const uint64_t L = (uint64_t)l0 | ((uint64_t)l1 << 32);
+            uint8_t* grp = ws + off_grp(j, DELTA);
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t i = lane + 32 * h;
+                if (lead2[h]) {
+                    const uint64_t rest = i + 1 < 64 ? (L >> (i + 1)) : 0ull;
+                    const uint32_t next = rest ? i + 1 + (uint32_t)__ffsll((long long)rest) - 1 : nj;
+                    grp[i] = (uint8_t)(next - i);
+                }
+            }
         }
         // inclusive scans of the two halves, then exclusive offsets
         uint64_t a = len2[0], b = len2[1];
@@ -311,10 +361,12 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             ip_[j] = 0;
         }
         __syncwarp();
+        // work units of the cost model count every prefix, also those whose
+        // extensions an aggregated group shares
         if (lane == 0 && count_stats) {
             stat_add(A.stats, 0, j, nj);
             stat_add(A.stats, 1, j, (unsigned long long)nj * P.nb[j]);
-            stat_add(A.stats, 2, j, total);
+            stat_add(A.stats, 2, j, aggm ? all2 : total);
         }
     };
 
@@ -457,6 +509,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     keep = DELTA ? gj_view_member(G, Dv, 0, P.sf_view[f], u, w)
                                  : gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
                 }
+                keep = keep && gj_lt_ok(P, 1, x1, [&](uint32_t) { return x0; });
             }
             if (k == 2) {
                 if (keep) {
@@ -513,10 +566,54 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const uint32_t nb = P.nb[j];
             const uint32_t a_new = P.order[j];
             uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA));
+            const uint8_t* grp = ws + off_grp(j, DELTA);
+            const bool agg = !DELTA && last && P.agg;
             constexpr int MAXO = 3;  // other binding lists cached for a step-uniform prefix
             const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
             uint32_t ol[MAXO], obits[MAXO];
             uint32_t cached = 0xffffffffu;
+            uint32_t lo_in = 0;         // the cached prefix's inequality bounds: lo_in <= e < hi_ex
+            uint64_t hi_ex = 1ull << 32;
+            // the other binding lists and the inequality bounds of prefix pi, in registers
+            auto cache_prefix = [&](uint32_t pi) {
+                const uint32_t b0 = minb[pi];
+                uint32_t o = 0;
+                for (uint32_t b = 0; b < nb; b++) {
+                    if (b == b0) continue;
+                    const BindList L =
+                        gj_bind_list(G, P.bdir[j][b], tup[P.bpos[j][b] * FC + pi], tup[P.bpos2[j][b] * FC + pi]);
+#pragma unroll
+                    for (int q = 0; q < MAXO; q++)
+                        if (q == (int)o) {
+                            ob[q] = L.bits ? L.tab : L.p;
+                            ol[q] = L.len;
+                            obits[q] = L.bits;
+                        }
+                    o++;
+                }
+                lo_in = 0;
+                hi_ex = 1ull << 32;
+                for (uint32_t c = 0; c < P.nlt[j]; c++) {
+                    const uint32_t v = tup[P.lt_pos[j][c] * FC + pi];
+                    if (P.lt_less[j][c]) hi_ex = v < hi_ex ? v : hi_ex;
+                    else lo_in = v + 1 > lo_in ? v + 1 : lo_in;
+                }
+                cached = pi;
+            };
+            // hashes the nsv buffered matches against every member of the group
+            // that starts at prefix g0 (g members): count += nsv * g
+            auto flush_group = [&](uint32_t g0, uint32_t g, uint32_t nsv) {
+                cnt += (unsigned long long)nsv * g;
+                for (uint32_t mbr = g0; mbr < g0 + g; mbr++) {
+                    const uint64_t hm = hpre[mbr];
+                    for (uint32_t t = lane; t < nsv; t += 32) {
+                        uint64_t h = gj_mix64(hm ^ (uint64_t)sv[t]);
+                        for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
+                        chk += h;
+                    }
+                }
+                __syncwarp();
+            };
             uint64_t cur = cur_[j];
             uint32_t ip = (uint32_t)ip_[j];
             uint32_t nn = last ? 0u : (uint32_t)n_[j + 1];
@@ -563,30 +660,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 if (!DELTA && last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
                     // Last level, next 64 candidates all in prefix ip: two per
                     // lane, with their probes interleaved.
-                    if (ip != cached) {
-                        const uint32_t b0 = minb[ip];
-                        uint32_t o = 0;
-                        for (uint32_t b = 0; b < nb; b++) {
-                            if (b == b0) continue;
-                            const uint32_t v = tup[P.bpos[j][b] * FC + ip];
-                            const uint32_t dir = P.bdir[j][b];
-                            const int64_t* off = dir ? G.ro : G.fo;
-                            const int64_t s0 = __ldg(off + v);
-                            const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s0);
-                            const bool hashed = len >= GJ_HASH_MIN_DEG;
-                            const uint32_t* p = hashed ? (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v)
-                                                       : (dir ? G.rn : G.fn) + s0;
-#pragma unroll
-                            for (int q = 0; q < MAXO; q++)
-                                if (q == (int)o) {
-                                    ob[q] = p;
-                                    ol[q] = len;
-                                    obits[q] = hashed ? gj_tab_bits(len) : 0u;
-                                }
-                            o++;
-                        }
-                        cached = ip;
-                    }
+                    if (ip != cached) cache_prefix(ip);
+                    const uint32_t gsz = agg ? grp[ip] : 1u;  // prefixes whose matches these candidates make
+                    uint32_t nsv = 0;
                     // Up to 16 steps on prefix ip alone, its invariants in
                     // registers and 32-bit offsets r into its min list. When
                     // the warp's range [cur, tot) ends inside prefix ip (its
@@ -605,6 +681,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         bool k0 = q0 < rend, k1 = q1 < rend;
                         const uint32_t e0 = k0 ? __ldg(ml + q0) : 0u;
                         const uint32_t e1 = k1 ? __ldg(ml + q1) : 0u;
+                        k0 = k0 && e0 >= lo_in && (uint64_t)e0 < hi_ex;
+                        k1 = k1 && e1 >= lo_in && (uint64_t)e1 < hi_ex;
 #pragma unroll
                         for (int q = 0; q < MAXO; q++) {
                             if (q + 1 < (int)nb) {
@@ -612,18 +690,33 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                                 else member32x2(ob[q], ol[q], e0, k0, e1, k1);
                             }
                         }
-                        if (k0 | k1) {
-                            uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
-                            for (uint32_t a = a_new + 1; a < k; a++) {
-                                const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
-                                h0 = gj_mix64(h0 ^ x);
-                                h1 = gj_mix64(h1 ^ x);
+                        if (gsz == 1) {
+                            if (k0 | k1) {
+                                uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
+                                for (uint32_t a = a_new + 1; a < k; a++) {
+                                    const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
+                                    h0 = gj_mix64(h0 ^ x);
+                                    h1 = gj_mix64(h1 ^ x);
+                                }
+                                chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
                             }
-                            chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
+                            cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                        } else {
+                            // an aggregated group: buffer the step's matches, hash
+                            // them against every member once 64 are waiting
+                            const uint32_t m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+                            if (k0) sv[nsv + __popc(m0 & lt)] = e0;
+                            if (k1) sv[nsv + __popc(m0) + __popc(m1 & lt)] = e1;
+                            nsv += __popc(m0) + __popc(m1);
+                            __syncwarp();
+                            if (nsv >= 64) {
+                                flush_group(ip, gsz, nsv);
+                                nsv = 0;
+                            }
                         }
-                        cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
                         r += 64;
                     } while (++steps < 16 && r < rend && (tail_ok || rend - r >= 64));
+                    if (nsv) flush_group(ip, gsz, nsv);
                     cur = c0 + r;
                     continue;
                 }
@@ -666,32 +759,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 } else if (keep) {
                     e = __ldg(mptr[i] + (t - cs[i]));
                 }
+                if (keep && P.nlt[j]) keep = gj_lt_ok(P, j, e, [&](uint32_t p) { return tup[p * FC + i]; });
                 if (DELTA) {
                 } else if (uni && nb - 1 <= (uint32_t)MAXO) {
-                    if (ip != cached) {
-                        const uint32_t b0 = minb[ip];
-                        uint32_t o = 0;
-                        for (uint32_t b = 0; b < nb; b++) {
-                            if (b == b0) continue;
-                            const uint32_t v = tup[P.bpos[j][b] * FC + ip];
-                            const uint32_t dir = P.bdir[j][b];
-                            const int64_t* off = dir ? G.ro : G.fo;
-                            const int64_t s0 = __ldg(off + v);
-                            const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s0);
-                            const bool hashed = len >= GJ_HASH_MIN_DEG;
-                            const uint32_t* p = hashed ? (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v)
-                                                       : (dir ? G.rn : G.fn) + s0;
-#pragma unroll
-                            for (int q = 0; q < MAXO; q++)
-                                if (q == (int)o) {
-                                    ob[q] = p;
-                                    ol[q] = len;
-                                    obits[q] = hashed ? gj_tab_bits(len) : 0u;
-                                }
-                            o++;
-                        }
-                        cached = ip;
-                    }
+                    if (ip != cached) cache_prefix(ip);
 #pragma unroll
                     for (int q = 0; q < MAXO; q++)
                         if (q + 1 < (int)nb && keep)
@@ -700,21 +771,27 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     const uint32_t b0 = minb[i];
                     for (uint32_t b = 0; b < nb && keep; b++) {
                         if (b == b0) continue;
-                        const uint32_t v = tup[P.bpos[j][b] * FC + i];
-                        keep = P.bdir[j][b] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
-                                            : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
+                        const BindList L =
+                            gj_bind_list(G, P.bdir[j][b], tup[P.bpos[j][b] * FC + i], tup[P.bpos2[j][b] * FC + i]);
+                        keep = gj_bind_member(L, e);
                     }
                 }
                 cur += 32;
                 if (last) {
+                    const uint32_t gsz = (agg && keep) ? grp[i] : 1u;  // members of an aggregated group
                     if (keep) {
-                        uint64_t h = gj_mix64(hpre[i] ^ (uint64_t)e);
-                        for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + i]);
-                        chk += (!DELTA || sg > 0) ? h : 0ull - h;
+                        for (uint32_t mbr = i; mbr < i + gsz; mbr++) {
+                            uint64_t h = gj_mix64(hpre[mbr] ^ (uint64_t)e);
+                            for (uint32_t a = a_new + 1; a < k; a++)
+                                h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
+                            chk += (!DELTA || sg > 0) ? h : 0ull - h;
+                        }
                     }
                     if (DELTA)
                         cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
                                __popc(__ballot_sync(0xffffffffu, keep && sg < 0));
+                    else if (agg)
+                        cnt += __reduce_add_sync(0xffffffffu, keep ? gsz : 0u);
                     else
                         cnt += __popc(__ballot_sync(0xffffffffu, keep));
                     continue;
@@ -1041,6 +1118,15 @@ int noalloc_scratch(gj_ctx* ctx, int dev, unsigned char** out) {
         return GJ_E_INVALID;
     }
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (g_noalloc_addr[dev]) {
+        // still this device's memory? (not after the process reset the device)
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, g_noalloc_addr[dev]) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
+            at.device != dev) {
+            cudaGetLastError();
+            g_noalloc_addr[dev] = nullptr;
+        }
+    }
     if (!g_noalloc_addr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -1076,15 +1162,17 @@ int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uin
     // the array keeps the previous call's contents: clear the counters this launch adds into
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(base + NA_COUNTS, 0, NA_END - NA_COUNTS, st));
     GraphView G = g->view();
-    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, g->n, seed_lo, seed_n, qbase);
+    k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, g->n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
     const int smem = gj_fused_smem_bytes(kmax);
     if (smem > 48 * 1024)
         GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
+    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    A.chunk = ctx->seed_chunk;
     k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
@@ -1103,6 +1191,9 @@ int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uin
         W.produced[j] = (int64_t)hs[3 * 9 + j];
     }
     W.seeds = (int64_t)hs[4 * 9 + 0];
+    int64_t total = 0;
+    for (uint32_t q = 0; q < nq; q++) total += counts[q];
+    W.produced[kmax] = total;
     return GJ_OK;
 }
 
@@ -1117,8 +1208,13 @@ extern "C" int gj_count_noalloc(gj_graph* g, const gj_query* const* qs, uint32_t
         gj_set_error(ctx, GJ_E_INVALID, "gj_count_noalloc: at most 64 queries per call");
         return GJ_E_INVALID;
     }
-    for (uint32_t i = 0; i < nq; i++)
+    for (uint32_t i = 0; i < nq; i++) {
         if (!qs[i] || qs[i]->ctx != ctx) return GJ_E_INVALID;
+        if (qs[i]->ntri && !g->tri.off) {  // building the triangle index would allocate
+            gj_set_error(ctx, GJ_E_INVALID, "gj_count_noalloc: build the triangle index first");
+            return GJ_E_INVALID;
+        }
+    }
     std::lock_guard<std::mutex> lk(ctx->mu);
     int prev = -1;
     cudaGetDevice(&prev);

@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, DeltaView D, D
                 uint32_t u = P.sf_dir[f] ? x1 : x0, w = P.sf_dir[f] ? x0 : x1;
                 keep = gj_view_member(G, Dv, 0, P.sf_view[f], u, w);
             }
+            keep = keep && gj_lt_ok(P, 1, x1, [&](uint32_t) { return x0; });
         }
         if (emit) {
             if (keep) {
@@ -124,10 +125,17 @@ __global__ void __launch_bounds__(PT) k_count(Plan P, GraphView G, DeltaView D, 
         uint32_t best = 0xffffffffu, space = 0, bi = 0;
         for (uint32_t b = 0; b < P.nb[j]; b++) {
             const uint32_t v = in.x[P.bpos[j][b]][i];
-            const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], v);
-            if (L.degree() < best) {
-                best = L.degree();
-                space = L.space();
+            uint32_t deg, sp;
+            if (P.bdir[j][b] == GJ_BIND_TRI) {  // static plans only
+                deg = sp = gj_bind_list(G, GJ_BIND_TRI, v, in.x[P.bpos2[j][b]][i]).len;
+            } else {
+                const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], v);
+                deg = L.degree();
+                sp = L.space();
+            }
+            if (deg < best) {
+                best = deg;
+                space = sp;
                 bi = b;
             }
         }
@@ -164,14 +172,23 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, DeltaView D,
             const uint32_t b = mini[i];
             for (uint32_t p = 0; p < j; p++) xs[p] = in.x[p][i];
             if (in.sg) sign = in.sg[i];
-            const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], xs[P.bpos[j][b]]);
-            const uint32_t e = r < L.base_len ? __ldg(L.base + r) : __ldg(L.ins + (r - L.base_len));
-            if (r < L.base_len && L.ndel) keep = !gj_contains(L.del, L.ndel, e);  // deleted in the new version
+            uint32_t e;
+            if (P.bdir[j][b] == GJ_BIND_TRI) {
+                e = __ldg(gj_bind_list(G, GJ_BIND_TRI, xs[P.bpos[j][b]], xs[P.bpos2[j][b]]).p + r);
+            } else {
+                const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], xs[P.bpos[j][b]]);
+                e = r < L.base_len ? __ldg(L.base + r) : __ldg(L.ins + (r - L.base_len));
+                if (r < L.base_len && L.ndel) keep = !gj_contains(L.del, L.ndel, e);  // deleted in the new version
+            }
             xs[j] = e;
             for (uint32_t bb = 0; bb < P.nb[j] && keep; bb++) {
                 if (bb == b) continue;
-                keep = gj_view_member(G, Dv, P.bdir[j][bb], P.bview[j][bb], xs[P.bpos[j][bb]], e);
+                if (P.bdir[j][bb] == GJ_BIND_TRI)
+                    keep = gj_bind_member(gj_bind_list(G, GJ_BIND_TRI, xs[P.bpos[j][bb]], xs[P.bpos2[j][bb]]), e);
+                else
+                    keep = gj_view_member(G, Dv, P.bdir[j][bb], P.bview[j][bb], xs[P.bpos[j][bb]], e);
             }
+            if (keep && P.nlt[j]) keep = gj_lt_ok(P, j, e, [&](uint32_t p) { return xs[p]; });
         }
         if (last) {
             if (keep) {

@@ -71,6 +71,17 @@ struct GraphView {
     const uint32_t* __restrict__ ft;
     const int64_t* __restrict__ rto;  // hash sets of the reverse lists
     const uint32_t* __restrict__ rt;
+    const int64_t* __restrict__ to;   // triangle lists per forward slot (null until built)
+    const uint32_t* __restrict__ tn;
+};
+
+// The ternary relation tri(a, b, c) (a -> b, a -> c, b -> c; Section 5.4)
+// indexed by its first two attributes: for the forward slot e of the edge
+// a -> b, the c are nbr[off[e] .. off[e+1]), ascending.
+struct gj_tri {
+    int64_t* off = nullptr;  // [m + 1]
+    uint32_t* nbr = nullptr; // [count]
+    uint64_t count = 0;
 };
 
 struct gj_graph {
@@ -81,9 +92,12 @@ struct gj_graph {
     uint64_t last_changes = 0;  // normalised changes of the last applied batch
     gj_csr fwd;  // out-neighbours
     gj_csr rev;  // in-neighbours
+    gj_tri tri;  // triangle index (built on request; dropped when the graph changes)
+    uint32_t* relabel = nullptr;  // new id of each input id (degree renaming), null = identity
+    uint32_t load_flags = 0;
     GraphView view() const {
         return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
-                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab};
+                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr};
     }
 };
 
@@ -91,31 +105,48 @@ struct gj_graph {
 
 // Execution plan of one query. Positions are places in the execution
 // (global attribute) order; x[p] is the value bound at position p.
+constexpr uint32_t GJ_MAX_LT = 8;  // inequality filters per level
+enum { GJ_BIND_FWD = 0, GJ_BIND_REV = 1, GJ_BIND_TRI = 2 };
 struct Plan {
     uint32_t k;
     uint32_t natoms;
     uint32_t qpos[GJ_MAX_K];    // qpos[a] = position of query attribute a (hash in query order)
     uint32_t order[GJ_MAX_K];   // order[p] = query attribute at position p
-    // Seed: edges of atom seed_atom give (x0, x1). seed_dir 0: the atom is
-    // E(x0, x1), read from the forward index keyed by x0; 1: E(x1, x0),
-    // read from the reverse index keyed by x0.
+    // Seed: edges (x0, x1) of the relation over the first two positions.
+    // seed_dir 0: edges x0 -> x1, read from the forward index keyed by x0;
+    // 1: edges x1 -> x0, read from the reverse index keyed by x0.
+    // seed_atom: the edge atom that gives them (delta plans: the atom whose
+    // changes seed dQ_i).
     uint32_t seed_atom;
     uint32_t seed_dir;
-    uint32_t nsf;                     // further atoms over {x0, x1}: membership filters
+    uint32_t nsf;                     // further edge atoms over {x0, x1}: membership filters
     uint8_t sf_dir[GJ_MAX_ATOMS];     // 0: edge x0->x1 must exist, 1: edge x1->x0
-    uint8_t sf_atom[GJ_MAX_ATOMS];
-    // Level p = 2..k-1 extends prefixes of length p by x_p. Binding atom b
-    // gives the list of x[bpos] in the forward index (bdir 0: atom
-    // E(x_bpos, x_p)) or reverse index (bdir 1: atom E(x_p, x_bpos)).
+    // Level p = 2..k-1 extends prefixes of length p by x_p. Binding b gives
+    // the list of x[bpos] in the forward index (bdir GJ_BIND_FWD: atom
+    // E(x_bpos, x_p)), in the reverse index (GJ_BIND_REV: atom E(x_p,
+    // x_bpos)), or the triangle list of the edge x[bpos] -> x[bpos2]
+    // (GJ_BIND_TRI: atom tri(x_bpos, x_bpos2, x_p), Section 5.4).
     uint32_t nb[GJ_MAX_K];
     uint8_t bpos[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t bpos2[GJ_MAX_K][GJ_MAX_ATOMS];
     uint8_t bdir[GJ_MAX_K][GJ_MAX_ATOMS];
-    uint8_t batom[GJ_MAX_K][GJ_MAX_ATOMS];
     // Delta queries (Section 3.3.1): which version each atom reads, 0 = the
     // committed graph (old), 1 = the committed graph plus the batch (new).
     // Static plans leave these 0.
     uint8_t bview[GJ_MAX_K][GJ_MAX_ATOMS];
     uint8_t sf_view[GJ_MAX_ATOMS];
+    // Inequality filters (Section 5.4) of level p: the new value x_p must be
+    // below (lt_less 1) or above (0) x[lt_pos]. Level 1 holds the filters
+    // between x1 and x0 (applied to the seeds).
+    uint8_t nlt[GJ_MAX_K];
+    uint8_t lt_pos[GJ_MAX_K][GJ_MAX_LT];
+    uint8_t lt_less[GJ_MAX_K][GJ_MAX_LT];
+    // Aggregation of identical lookups at the last level (the aggregation of
+    // requests with equal keys of Section 3.4.2): bit p is set if the last
+    // level's lists or filters read x_p. Prefixes that agree on those
+    // positions have the same extensions, so consecutive ones are extended
+    // once. 0: off (some list reads every earlier position, or delta plans).
+    uint32_t agg;
     uint32_t delta;  // 1: seeds are the batch's signed changes of atom seed_atom
 };
 
@@ -152,15 +183,18 @@ struct DeltaBatch {
 
 struct gj_query {
     gj_ctx* ctx = nullptr;
-    uint32_t k = 0, natoms = 0;
+    uint32_t k = 0, natoms = 0, ntri = 0, nlt = 0;
     uint32_t as[GJ_MAX_ATOMS], ad[GJ_MAX_ATOMS];
+    uint32_t ta[GJ_MAX_ATOMS], tb[GJ_MAX_ATOMS], tc[GJ_MAX_ATOMS];  // tri atoms
+    uint32_t la[GJ_MAX_ATOMS], lb[GJ_MAX_ATOMS];                    // x_la < x_lb
     uint32_t order[GJ_MAX_K];
     Plan plan;
-    Plan dplan[GJ_MAX_ATOMS];  // delta queries dQ_i, one per atom
+    Plan dplan[GJ_MAX_ATOMS];  // delta queries dQ_i, one per atom (edge-atom queries only)
 };
 
-int gj_plan_compile(const uint32_t* as, const uint32_t* ad, uint32_t natoms, uint32_t k, const uint32_t* order,
-                    Plan* out, std::string* why);
+// Plan of q's static evaluation in q->order (q's atoms, tri atoms and
+// inequalities set; q->order the global order).
+int gj_plan_compile(const gj_query* q, Plan* out, std::string* why);
 // Plan of delta query dQ_i of q (Section 3.3.1): seeded from the changes of
 // atom i, atoms before i read the new version, atoms after i the old one.
 int gj_plan_compile_delta(const gj_query* q, uint32_t i, Plan* out, std::string* why);
@@ -226,6 +260,13 @@ int gj_radix_sort_kv(gj_ctx* ctx, uint64_t* keys, uint64_t* ktmp, uint32_t* vals
                      uint64_t** kresult, uint32_t** vresult);
 
 int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint64_t m, uint32_t n, gj_graph* g);
+// Symmetry breaking's input transformation (Section 5.4) on a built graph:
+// rebuilds g with the flags of gj_graph_load_ex (symmetrise, rename by
+// degree, orient from lower to higher id).
+int gj_graph_transform(gj_ctx* ctx, gj_graph* g, uint32_t flags);
+// Builds g's triangle index (Section 5.4) if it is missing.
+int gj_tri_build(gj_ctx* ctx, gj_graph* g);
+void gj_tri_release(gj_tri& t);
 // Offsets and hash sets of an index whose key/nbr arrays (mu sorted slots) are set.
 int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out);
 
@@ -432,6 +473,61 @@ __device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaVi
         if (gj_contains(S.del_nbr + r.z, r.w - r.z, x)) return false;
     }
     return dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
+}
+
+// Position of e in the sorted list a[0, len), or -1: branch-free binary
+// search over power-of-two steps.
+__device__ __forceinline__ int64_t gj_find(const uint32_t* __restrict__ a, uint32_t len, uint32_t e) {
+    if (len == 0) return -1;
+    uint32_t step = 1u << (31 - __clz(len));
+    uint32_t pos = (__ldg(a + (len - step)) <= e) ? len - step : 0u;
+    for (step >>= 1; step; step >>= 1) {
+        const uint32_t q = pos + step;
+        pos = (__ldg(a + q) <= e) ? q : pos;
+    }
+    return __ldg(a + pos) == e ? (int64_t)pos : -1;
+}
+
+// The list a binding of a plan level reads for one prefix (static plans):
+// the sorted list p[0, len) and, for long index lists, its hash set (bits
+// > 0). v is x[bpos]; v2 is x[bpos2] (tri bindings only).
+struct BindList {
+    const uint32_t* p;
+    uint32_t len;
+    const uint32_t* tab;
+    uint32_t bits;
+};
+
+__device__ __forceinline__ BindList gj_bind_list(const GraphView& G, uint32_t dir, uint32_t v, uint32_t v2) {
+    if (dir == GJ_BIND_TRI) {
+        // the triangles on the edge v -> v2: find its forward slot, then its list
+        const int64_t s = __ldg(G.fo + v);
+        const int64_t e = gj_find(G.fn + s, (uint32_t)(__ldg(G.fo + v + 1) - s), v2);
+        if (e < 0) return BindList{G.fn, 0u, nullptr, 0u};
+        const int64_t a = __ldg(G.to + s + e);
+        return BindList{G.tn + a, (uint32_t)(__ldg(G.to + s + e + 1) - a), nullptr, 0u};
+    }
+    const int64_t* off = dir ? G.ro : G.fo;
+    const int64_t s = __ldg(off + v);
+    const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s);
+    const uint32_t* p = (dir ? G.rn : G.fn) + s;
+    if (len >= GJ_HASH_MIN_DEG) return BindList{p, len, (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v), gj_tab_bits(len)};
+    return BindList{p, len, nullptr, 0u};
+}
+
+__device__ __forceinline__ bool gj_bind_member(const BindList& L, uint32_t e) {
+    return L.bits ? gj_tab_member(L.tab, L.bits, e) : gj_contains(L.p, L.len, e);
+}
+
+// Whether the value e of position j meets level j's inequality filters;
+// val(p) gives the prefix's value at position p.
+template <class F>
+__device__ __forceinline__ bool gj_lt_ok(const Plan& P, uint32_t j, uint32_t e, F val) {
+    for (uint32_t c = 0; c < P.nlt[j]; c++) {
+        const uint32_t v = val(P.lt_pos[j][c]);
+        if (P.lt_less[j][c] ? !(e < v) : !(e > v)) return false;
+    }
+    return true;
 }
 
 __device__ __forceinline__ uint32_t gj_lanemask_lt() {

@@ -351,7 +351,7 @@ int gj_submit_count(gj_ctx* ctx, const gj_query* const* qs, uint32_t nq, uint64_
     Request* r = new (std::nothrow) Request();
     if (!r) return GJ_E_NOMEM;
     for (uint32_t i = 0; i < nq; i++) {
-        if (!qs[i] || qs[i]->ctx != ctx) {
+        if (!qs[i] || qs[i]->ctx != ctx || qs[i]->ntri) {  // the triangle index is not versioned: no tri atoms
             delete r;
             return GJ_E_INVALID;
         }
@@ -379,7 +379,7 @@ int gj_submit_batch(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, const
     Request* r = new (std::nothrow) Request();
     if (!r) return GJ_E_NOMEM;
     for (uint32_t i = 0; i < nq; i++) {
-        if (!qs[i] || qs[i]->ctx != ctx) {
+        if (!qs[i] || qs[i]->ctx != ctx || qs[i]->ntri) {  // the triangle index is not versioned: no tri atoms
             delete r;
             return GJ_E_INVALID;
         }

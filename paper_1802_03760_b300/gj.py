@@ -21,6 +21,9 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gj.h")
 ENGINE_PLAIN = 0
 ENGINE_FUSED = 1
 FLAG_DELTA_FUSED = 1
+LOAD_SYMMETRIZE = 1
+LOAD_DEGREE_ORDER = 2
+LOAD_ORIENT = 4
 
 ERRORS = {
     -1: "GJ_E_INVALID", -2: "GJ_E_RANGE", -3: "GJ_E_NOMEM", -4: "GJ_E_ADMIT", -5: "GJ_E_TRUNCATED",
@@ -84,10 +87,16 @@ _SIGS = {
     "gj_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "gj_last_error": (ctypes.c_char_p, [_VP]),
     "gj_graph_load": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.POINTER(_VP)]),
+    "gj_graph_load_ex": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                        ctypes.POINTER(_VP)]),
+    "gj_graph_relabel_map": (ctypes.c_int, [_VP, _U32P]),
+    "gj_graph_build_triangles": (ctypes.c_int, [_VP, _U64P]),
     "gj_graph_stats": (ctypes.c_int, [_VP, _U64P, _U64P]),
     "gj_graph_export": (ctypes.c_int, [_VP, _I64P, _U32P]),
     "gj_graph_free": (None, [_VP]),
     "gj_query_define": (ctypes.c_int, [_VP, ctypes.c_uint32, _U32P, ctypes.c_uint32, _U32P, ctypes.POINTER(_VP)]),
+    "gj_query_define_ex": (ctypes.c_int, [_VP, ctypes.c_uint32, _U32P, ctypes.c_uint32, _U32P, ctypes.c_uint32, _U32P,
+                                          ctypes.c_uint32, _U32P, ctypes.POINTER(_VP)]),
     "gj_query_free": (None, [_VP]),
     "gj_count": (ctypes.c_int, [_VP, _VP, _I64P, _U64P]),
     "gj_count_ex": (ctypes.c_int, [_VP, _VP, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _I64P, _U64P,
@@ -151,6 +160,11 @@ def _ptr(a, elem: int = 4):
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         if a.dim() != 1 or not a.is_contiguous() or a.element_size() != elem:
             raise ValueError("tensor arguments must be 1-D, contiguous, with %d-byte elements" % elem)
+        if a.is_cuda:
+            # the library reads device inputs on its own stream: the work that
+            # wrote this tensor (on the current stream) must have finished
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
         return ctypes.c_void_p(a.data_ptr()), a
     arr = np.ascontiguousarray(a, dtype=np.uint32 if elem == 4 else np.int8)
     if arr.ndim != 1:
@@ -185,6 +199,7 @@ class Context:
         h = _VP()
         _check(lib().gj_create(device, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+        self.device = device
         self._children = weakref.WeakSet()  # graphs and queries, freed before the context
 
     def close(self):
@@ -226,18 +241,37 @@ class Context:
         return w
 
 
+def _check_device(ctx, *arrays):
+    """Device tensors must be on the context's device (the library refuses others)."""
+    for a in arrays:
+        if a is not None and getattr(a, "is_cuda", False) and a.device.index != ctx.device:
+            raise ValueError("tensor on cuda:%d, context on cuda:%d" % (a.device.index, ctx.device))
+
+
 class Graph:
-    def __init__(self, ctx: Context, src, dst, num_vertices: int):
+    def __init__(self, ctx: Context, src, dst, num_vertices: int, flags: int = 0):
         self.ctx = ctx
         self._h = None
+        _check_device(ctx, src, dst)
         ps, ks = _ptr(src)
         pd, kd = _ptr(dst)
         m = _same_length(ks, kd)
         h = _VP()
-        _check(lib().gj_graph_load(ctx._h, ps, pd, m, num_vertices, ctypes.byref(h)), ctx)
+        _check(lib().gj_graph_load_ex(ctx._h, ps, pd, m, num_vertices, flags, ctypes.byref(h)), ctx)
         self._h = h
         self.n = num_vertices
         ctx._children.add(self)
+
+    def relabel_map(self):
+        """new_of_old: the id each input vertex has in the graph's indices."""
+        m = np.empty(max(self.n, 1), np.uint32)
+        _check(lib().gj_graph_relabel_map(self._h, m.ctypes.data_as(_U32P)), self.ctx)
+        return m[:self.n]
+
+    def build_triangles(self) -> int:
+        c = ctypes.c_uint64(0)
+        _check(lib().gj_graph_build_triangles(self._h, ctypes.byref(c)), self.ctx)
+        return c.value
 
     def free(self):
         if self._h:
@@ -268,16 +302,22 @@ class Graph:
 
 
 class Query:
-    def __init__(self, ctx: Context, k: int, atoms, order=None):
+    def __init__(self, ctx: Context, k: int, atoms, order=None, tri=(), lt=()):
         self.ctx = ctx
         self._h = None
         self.k = k
         self.atoms = [tuple(a) for a in atoms]
-        flat = np.array([x for a in self.atoms for x in a], dtype=np.uint32)
+        self.tri = [tuple(t) for t in tri]
+        self.lt = [tuple(c) for c in lt]
+        flat = np.array([x for a in self.atoms for x in a] or [0], dtype=np.uint32)
+        ft = np.array([x for t in self.tri for x in t] or [0], dtype=np.uint32)
+        fl = np.array([x for c in self.lt for x in c] or [0], dtype=np.uint32)
         o = np.array(order, dtype=np.uint32) if order is not None else None
         h = _VP()
-        _check(lib().gj_query_define(ctx._h, k, flat.ctypes.data_as(_U32P), len(self.atoms),
-                                     o.ctypes.data_as(_U32P) if o is not None else None, ctypes.byref(h)), ctx)
+        _check(lib().gj_query_define_ex(ctx._h, k, flat.ctypes.data_as(_U32P) if self.atoms else None, len(self.atoms),
+                                        ft.ctypes.data_as(_U32P) if self.tri else None, len(self.tri),
+                                        fl.ctypes.data_as(_U32P) if self.lt else None, len(self.lt),
+                                        o.ctypes.data_as(_U32P) if o is not None else None, ctypes.byref(h)), ctx)
         self._h = h
         ctx._children.add(self)
 
@@ -356,6 +396,7 @@ def _ptr8(a):
 
 def apply_batch(g: Graph, src, dst, sign, qs=()):
     """Applies one update batch; returns ([delta counts], [delta checksums]) of qs."""
+    _check_device(g.ctx, src, dst, sign)
     ps, ks = _ptr(src)
     pd, kd = _ptr(dst)
     pg, kg = _ptr8(sign)

@@ -65,3 +65,29 @@ def test_marshalling_rejects_arrays_the_library_would_misread():
         gj._ptr8(t)
     p8, keep8 = gj._ptr8([1, -1, 1])
     assert keep8.dtype == np.int8 and keep8.tolist() == [1, -1, 1]
+
+
+def test_tensor_on_another_device_is_refused_before_any_call():
+    """A device tensor on a GPU other than the context's is refused by the
+    binding (the library refuses it too): reading another GPU's memory without
+    peer access would fault."""
+    import types
+
+    class FakeDeviceTensor:
+        is_cuda = True
+        device = types.SimpleNamespace(index=1)
+
+    ctx = types.SimpleNamespace(device=0, _h=None)
+    with pytest.raises(ValueError, match="cuda:1"):
+        gj.Graph(ctx, FakeDeviceTensor(), FakeDeviceTensor(), 10)
+    g = types.SimpleNamespace(ctx=ctx, _h=None)
+    with pytest.raises(ValueError, match="cuda:1"):
+        gj.apply_batch(g, FakeDeviceTensor(), None, None)
+
+
+def test_load_and_query_extensions_reject_bad_arguments_without_device_work():
+    L = gj.lib()
+    assert L.gj_graph_load_ex(None, None, None, 0, 10, 0, None) == -1
+    assert L.gj_query_define_ex(None, 3, None, 0, None, 0, None, 0, None, None) == -1
+    assert L.gj_graph_build_triangles(None, None) == -1
+    assert L.gj_graph_relabel_map(None, None) == -1
