@@ -487,8 +487,12 @@ int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t
     int per_sm_max = 0;
     {
         uint32_t kmax = 2;
-        for (uint32_t i = 0; i < nq; i++) kmax = qs[i]->k > kmax ? qs[i]->k : kmax;
-        per_sm_max = gj_fused_occupancy(ctx, kmax);
+        bool ext = false;
+        for (uint32_t i = 0; i < nq; i++) {
+            kmax = qs[i]->k > kmax ? qs[i]->k : kmax;
+            ext = ext || gj_plan_ext(qs[i]->plan);
+        }
+        per_sm_max = gj_fused_occupancy(ctx, kmax, ext);
     }
     double best_f = 1e300;
     uint32_t best_chunk = 32, best_bps = 0;

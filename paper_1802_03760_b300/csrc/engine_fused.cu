@@ -88,36 +88,43 @@ constexpr uint32_t IDLE_WAIT_LIMIT = 1u << 26;  // iterations of the idle wait b
 constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
-// Matches of an aggregated last-level group wait here until 64 or more can
-// be hashed against every member of the group at once.
-constexpr uint32_t SV_CAP = 128;
+// Matches of an aggregated last-level group wait here until 32 or more can
+// be hashed against every member of the group at once (EXT launches only).
+constexpr uint32_t SV_CAP = 96;
 constexpr uint32_t SV_BYTES = SV_CAP * 4;
-constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC + FC;  // mptr + cs + hpre + minb + grp
+static_assert(31 + 2 * 32 <= SV_CAP, "a step adds up to 64 matches to fewer than 32 buffered ones");
+constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC;  // mptr + cs + hpre + minb
+// EXT launches also keep the size of each aggregated group (at its leader).
+constexpr uint32_t GRP_BYTES = FC;
 // Delta plans also keep, per prefix, the new-version parts of the min list
 // (inserts, deletes, committed length) and the seed's sign.
 constexpr uint32_t LVL_DELTA = FC * 8 + FC * 8 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
-__host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d) { return LVL_FIXED + (d ? ALIGN16(LVL_DELTA) : 0); }
-__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d = false) {
+__host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d, bool x) {
+    return LVL_FIXED + (x ? GRP_BYTES : 0) + (d ? ALIGN16(LVL_DELTA) : 0);
+}
+__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d, bool x) {
     // sum over i = 2..j-1 of (FC * i * 4 + fixed part)
-    return PLAN_BYTES + SCAL_BYTES + SV_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) +
-           lvl_size_fixed(d) * (j - 2);
+    return PLAN_BYTES + SCAL_BYTES + (x ? SV_BYTES : 0) + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) +
+           lvl_size_fixed(d, x) * (j - 2);
 }
-__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d = false) { return lvl_base(j, d); }
-__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d = false) { return lvl_base(j, d) + FC * 4 * j; }
-__host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j, bool d = false) { return off_mptr(j, d) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j, bool d = false) {
-    return off_cs(j, d) + ALIGN16((FC + 1) * 8);
+__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d, bool x) { return lvl_base(j, d, x); }
+__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d, bool x) {
+    return lvl_base(j, d, x) + FC * 4 * j;
 }
-__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d = false) { return off_hpre(j, d) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j, bool d, bool x) { return off_mptr(j, d, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j, bool d, bool x) {
+    return off_cs(j, d, x) + ALIGN16((FC + 1) * 8);
+}
+__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d, bool x) { return off_hpre(j, d, x) + FC * 8; }
 // group size of an aggregated last-level prefix (leaders only)
-__host__ __device__ __forceinline__ uint32_t off_grp(uint32_t j, bool d = false) { return off_minb(j, d) + FC; }
-__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j) { return off_grp(j, true) + FC; }
-__host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j) { return off_dins(j) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j) { return off_ddel(j) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j) { return off_dblen(j) + FC * 4; }
-__host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j) { return off_dndel(j) + FC * 4; }
-__host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d = false) {
-    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES + SV_BYTES : lvl_base(kmax, d);
+__host__ __device__ __forceinline__ uint32_t off_grp(uint32_t j, bool d, bool x) { return off_minb(j, d, x) + FC; }
+__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j, bool x) { return off_minb(j, true, x) + FC + (x ? GRP_BYTES : 0); }
+__host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j, bool x) { return off_dins(j, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j, bool x) { return off_ddel(j, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j, bool x) { return off_dblen(j, x) + FC * 4; }
+__host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j, bool x) { return off_dndel(j, x) + FC * 4; }
+__host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d, bool x) {
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES + (x ? SV_BYTES : 0) : lvl_base(kmax, d, x);
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
@@ -200,13 +207,16 @@ __global__ void k_queue_init(unsigned long long* seq, uint32_t cap) {
 // DELTA: every plan is a delta query dQ_i (Section 3.3.1): seeds are the
 // batch's signed changes, atoms read the old or the new version, and each
 // prefix carries its seed's sign into the counts and checksums.
-template <bool DELTA>
+// EXT: some plan of the launch has tri atoms, inequality filters or an
+// aggregated last level (Section 5.4, Section 3.4.2); without them those
+// paths are compiled out.
+template <bool DELTA, bool EXT>
 __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const uint32_t lt = gj_lanemask_lt();
-    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes(A.kmax, DELTA);
+    unsigned char* ws = smem_raw + (size_t)warp * warp_bytes(A.kmax, DELTA, EXT);
     Plan& P = *reinterpret_cast<Plan*>(ws);
     uint64_t* n_ = reinterpret_cast<uint64_t*>(ws + PLAN_BYTES);
     uint64_t* cur_ = n_ + GJ_MAX_K;
@@ -242,17 +252,17 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     // the new one in query order (the tuple hash is a left fold).
     auto activate = [&](int j, bool count_stats = true) {
         const uint32_t nj = (uint32_t)n_[j];
-        uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j, DELTA));
-        const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j, DELTA));
-        uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j, DELTA));
-        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j, DELTA));
-        uint8_t* minb = ws + off_minb(j, DELTA);
+        uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j, DELTA, EXT));
+        const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j, DELTA, EXT));
+        uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j, DELTA, EXT));
+        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j, DELTA, EXT));
+        uint8_t* minb = ws + off_minb(j, DELTA, EXT);
         const bool last = (j == (int)k - 1);
         const uint32_t a_new = P.order[j];
         // aggregation: a prefix that agrees with the one before it on every
         // position the last level reads has the same extensions; it joins
         // that prefix's group and proposes nothing itself
-        const uint32_t aggm = (!DELTA && last) ? P.agg : 0u;
+        const uint32_t aggm = (EXT && !DELTA && last) ? P.agg : 0u;
         uint64_t len2[2];
         uint64_t all2 = 0;  // the min counts of every prefix, members of groups included
         bool lead2[2];
@@ -287,17 +297,17 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     }
                     best = bl.space();
                     bp = bl.base;
-                    reinterpret_cast<const uint32_t**>(ws + off_dins(j))[i] = bl.ins;
-                    reinterpret_cast<const uint32_t**>(ws + off_ddel(j))[i] = bl.del;
-                    reinterpret_cast<uint32_t*>(ws + off_dblen(j))[i] = bl.base_len;
-                    reinterpret_cast<uint32_t*>(ws + off_dndel(j))[i] = bl.ndel;
+                    reinterpret_cast<const uint32_t**>(ws + off_dins(j, EXT))[i] = bl.ins;
+                    reinterpret_cast<const uint32_t**>(ws + off_ddel(j, EXT))[i] = bl.del;
+                    reinterpret_cast<uint32_t*>(ws + off_dblen(j, EXT))[i] = bl.base_len;
+                    reinterpret_cast<uint32_t*>(ws + off_dndel(j, EXT))[i] = bl.ndel;
                 } else {
                     for (uint32_t b = 0; b < P.nb[j]; b++) {
                         uint32_t v = tup[P.bpos[j][b] * FC + i];
                         const uint32_t dir = P.bdir[j][b];
                         uint64_t len;
                         const uint32_t* lp;
-                        if (dir == GJ_BIND_TRI) {
+                        if (EXT && dir == GJ_BIND_TRI) {
                             const BindList L = gj_bind_list(G, dir, v, tup[P.bpos2[j][b] * FC + i]);
                             len = L.len;
                             lp = L.p;
@@ -331,7 +341,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         if (aggm) {
             const uint32_t l0 = __ballot_sync(0xffffffffu, lead2[0]), l1 = __ballot_sync(0xffffffffu, lead2[1]);
             const uint64_t L = (uint64_t)l0 | ((uint64_t)l1 << 32);
-            uint8_t* grp = ws + off_grp(j, DELTA);
+            uint8_t* grp = ws + off_grp(j, DELTA, EXT);
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const uint32_t i = lane + 32 * h;
@@ -439,11 +449,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     k = P.k;
                 }
                 const uint32_t L = Bd.level, nb_ = Bd.n;
-                uint32_t* tupL = reinterpret_cast<uint32_t*>(ws + off_tup(L, DELTA));
+                uint32_t* tupL = reinterpret_cast<uint32_t*>(ws + off_tup(L, DELTA, EXT));
                 for (uint32_t c = 0; c < L; c++)
                     for (uint32_t i = lane; i < nb_; i += 32) tupL[c * FC + i] = Bd.tup[c][i];
                 if (DELTA)
-                    for (uint32_t i = lane; i < nb_; i += 32) reinterpret_cast<int8_t*>(ws + off_dsg(L))[i] = Bd.sg[i];
+                    for (uint32_t i = lane; i < nb_; i += 32) reinterpret_cast<int8_t*>(ws + off_dsg(L, EXT))[i] = Bd.sg[i];
                 const unsigned long long c_lo = Bd.c_lo, c_hi = Bd.c_hi;
                 __syncwarp();
                 if (lane == 0) {
@@ -509,7 +519,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     keep = DELTA ? gj_view_member(G, Dv, 0, P.sf_view[f], u, w)
                                  : gj_list_member(G.fo, G.fn, G.fto, G.ft, u, w);
                 }
-                keep = keep && gj_lt_ok(P, 1, x1, [&](uint32_t) { return x0; });
+                if (EXT) keep = keep && gj_lt_ok(P, 1, x1, [&](uint32_t) { return x0; });
             }
             if (k == 2) {
                 if (keep) {
@@ -528,10 +538,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             uint32_t n2 = (uint32_t)n_[2];
             if (keep) {
                 uint32_t slot = n2 + __popc(mask & lt);
-                uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(2, DELTA));
+                uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(2, DELTA, EXT));
                 tup[0 * FC + slot] = x0;
                 tup[1 * FC + slot] = x1;
-                if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(2))[slot] = sg;
+                if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(2, EXT))[slot] = sg;
             }
             __syncwarp();
             if (lane == 0) {
@@ -557,17 +567,17 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         if (cur_[j] < tot_[j]) {
             uint64_t tot = tot_[j];
             const uint32_t nj = (uint32_t)n_[j];
-            const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA));
-            const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA));
-            const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j, DELTA));
-            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j, DELTA));
-            const uint8_t* minb = ws + off_minb(j, DELTA);
+            const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA, EXT));
+            const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA, EXT));
+            const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j, DELTA, EXT));
+            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j, DELTA, EXT));
+            const uint8_t* minb = ws + off_minb(j, DELTA, EXT);
             const bool last = (j == (int)k - 1);
             const uint32_t nb = P.nb[j];
             const uint32_t a_new = P.order[j];
-            uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA));
-            const uint8_t* grp = ws + off_grp(j, DELTA);
-            const bool agg = !DELTA && last && P.agg;
+            uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA, EXT));
+            const uint8_t* grp = ws + off_grp(j, DELTA, EXT);
+            const bool agg = EXT && !DELTA && last && P.agg;
             constexpr int MAXO = 3;  // other binding lists cached for a step-uniform prefix
             const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
             uint32_t ol[MAXO], obits[MAXO];
@@ -580,8 +590,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 uint32_t o = 0;
                 for (uint32_t b = 0; b < nb; b++) {
                     if (b == b0) continue;
-                    const BindList L =
-                        gj_bind_list(G, P.bdir[j][b], tup[P.bpos[j][b] * FC + pi], tup[P.bpos2[j][b] * FC + pi]);
+                    const uint32_t dir = EXT ? P.bdir[j][b] : (P.bdir[j][b] & 1u);
+                    const BindList L = gj_bind_list(G, dir, tup[P.bpos[j][b] * FC + pi], tup[P.bpos2[j][b] * FC + pi]);
 #pragma unroll
                     for (int q = 0; q < MAXO; q++)
                         if (q == (int)o) {
@@ -593,7 +603,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
                 lo_in = 0;
                 hi_ex = 1ull << 32;
-                for (uint32_t c = 0; c < P.nlt[j]; c++) {
+                for (uint32_t c = 0; EXT && c < P.nlt[j]; c++) {
                     const uint32_t v = tup[P.lt_pos[j][c] * FC + pi];
                     if (P.lt_less[j][c]) hi_ex = v < hi_ex ? v : hi_ex;
                     else lo_in = v + 1 > lo_in ? v + 1 : lo_in;
@@ -642,7 +652,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             for (uint32_t i2 = lane; i2 < nj; i2 += 32) Bd.tup[c][i2] = tup[c * FC + i2];
                         if (DELTA)
                             for (uint32_t i2 = lane; i2 < nj; i2 += 32)
-                                Bd.sg[i2] = reinterpret_cast<const int8_t*>(ws + off_dsg(j))[i2];
+                                Bd.sg[i2] = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[i2];
                         if (lane == 0) {
                             Bd.plan = (uint32_t)cur_q;
                             Bd.level = (uint32_t)j;
@@ -661,7 +671,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     // Last level, next 64 candidates all in prefix ip: two per
                     // lane, with their probes interleaved.
                     if (ip != cached) cache_prefix(ip);
-                    const uint32_t gsz = agg ? grp[ip] : 1u;  // prefixes whose matches these candidates make
+                    const uint32_t gsz = (EXT && agg) ? grp[ip] : 1u;  // prefixes whose matches these candidates make
                     uint32_t nsv = 0;
                     // Up to 16 steps on prefix ip alone, its invariants in
                     // registers and 32-bit offsets r into its min list. When
@@ -681,8 +691,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         bool k0 = q0 < rend, k1 = q1 < rend;
                         const uint32_t e0 = k0 ? __ldg(ml + q0) : 0u;
                         const uint32_t e1 = k1 ? __ldg(ml + q1) : 0u;
-                        k0 = k0 && e0 >= lo_in && (uint64_t)e0 < hi_ex;
-                        k1 = k1 && e1 >= lo_in && (uint64_t)e1 < hi_ex;
+                        if (EXT) {
+                            k0 = k0 && e0 >= lo_in && (uint64_t)e0 < hi_ex;
+                            k1 = k1 && e1 >= lo_in && (uint64_t)e1 < hi_ex;
+                        }
 #pragma unroll
                         for (int q = 0; q < MAXO; q++) {
                             if (q + 1 < (int)nb) {
@@ -690,7 +702,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                                 else member32x2(ob[q], ol[q], e0, k0, e1, k1);
                             }
                         }
-                        if (gsz == 1) {
+                        if (!EXT || gsz == 1) {
                             if (k0 | k1) {
                                 uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
                                 for (uint32_t a = a_new + 1; a < k; a++) {
@@ -703,20 +715,20 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
                         } else {
                             // an aggregated group: buffer the step's matches, hash
-                            // them against every member once 64 are waiting
+                            // them against every member once 32 are waiting
                             const uint32_t m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
                             if (k0) sv[nsv + __popc(m0 & lt)] = e0;
                             if (k1) sv[nsv + __popc(m0) + __popc(m1 & lt)] = e1;
                             nsv += __popc(m0) + __popc(m1);
                             __syncwarp();
-                            if (nsv >= 64) {
+                            if (nsv >= 32) {  // at most 31 + 64 < SV_CAP are ever buffered
                                 flush_group(ip, gsz, nsv);
                                 nsv = 0;
                             }
                         }
                         r += 64;
                     } while (++steps < 16 && r < rend && (tail_ok || rend - r >= 64));
-                    if (nsv) flush_group(ip, gsz, nsv);
+                    if (EXT && nsv) flush_group(ip, gsz, nsv);
                     cur = c0 + r;
                     continue;
                 }
@@ -739,16 +751,16 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     if (keep) {
                         // element r of the min list's new-version enumeration space
                         const uint32_t r = (uint32_t)(t - cs[i]);
-                        const uint32_t blen = reinterpret_cast<const uint32_t*>(ws + off_dblen(j))[i];
-                        const uint32_t ndel = reinterpret_cast<const uint32_t*>(ws + off_dndel(j))[i];
+                        const uint32_t blen = reinterpret_cast<const uint32_t*>(ws + off_dblen(j, EXT))[i];
+                        const uint32_t ndel = reinterpret_cast<const uint32_t*>(ws + off_dndel(j, EXT))[i];
                         if (r < blen) {
                             e = __ldg(mptr[i] + r);
                             if (ndel)
-                                keep = !gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j))[i], ndel, e);
+                                keep = !gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j, EXT))[i], ndel, e);
                         } else {
-                            e = __ldg(reinterpret_cast<const uint32_t* const*>(ws + off_dins(j))[i] + (r - blen));
+                            e = __ldg(reinterpret_cast<const uint32_t* const*>(ws + off_dins(j, EXT))[i] + (r - blen));
                         }
-                        sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j))[i];
+                        sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[i];
                         const uint32_t b0 = minb[i];
                         for (uint32_t b = 0; b < nb && keep; b++) {
                             if (b == b0) continue;
@@ -759,7 +771,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 } else if (keep) {
                     e = __ldg(mptr[i] + (t - cs[i]));
                 }
-                if (keep && P.nlt[j]) keep = gj_lt_ok(P, j, e, [&](uint32_t p) { return tup[p * FC + i]; });
+                if (EXT && keep && P.nlt[j]) keep = gj_lt_ok(P, j, e, [&](uint32_t p) { return tup[p * FC + i]; });
                 if (DELTA) {
                 } else if (uni && nb - 1 <= (uint32_t)MAXO) {
                     if (ip != cached) cache_prefix(ip);
@@ -767,18 +779,38 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     for (int q = 0; q < MAXO; q++)
                         if (q + 1 < (int)nb && keep)
                             keep = obits[q] ? gj_tab_member(ob[q], obits[q], e) : member32(ob[q], ol[q], e);
+                } else if (EXT) {
+                    // The lanes of one prefix look its lists up once: the first
+                    // lane of each run of equal prefixes resolves them and the
+                    // others read the result (aggregation of identical lookups).
+                    const uint32_t b0 = minb[i];
+                    const uint32_t prev = __shfl_up_sync(0xffffffffu, i, 1);
+                    const bool head = lane == 0 || prev != i;
+                    const int src = 31 - __clz(__ballot_sync(0xffffffffu, head) & (lt | (1u << lane)));
+                    for (uint32_t b = 0; b < nb; b++) {
+                        BindList L{nullptr, 0u, nullptr, 0u};
+                        if (head && b != b0)
+                            L = gj_bind_list(G, P.bdir[j][b], tup[P.bpos[j][b] * FC + i], tup[P.bpos2[j][b] * FC + i]);
+                        L.p = reinterpret_cast<const uint32_t*>(
+                            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(L.p), src));
+                        L.tab = reinterpret_cast<const uint32_t*>(
+                            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(L.tab), src));
+                        L.len = __shfl_sync(0xffffffffu, L.len, src);
+                        L.bits = __shfl_sync(0xffffffffu, L.bits, src);
+                        if (keep && b != b0) keep = gj_bind_member(L, e);
+                    }
                 } else if (keep) {
                     const uint32_t b0 = minb[i];
                     for (uint32_t b = 0; b < nb && keep; b++) {
                         if (b == b0) continue;
-                        const BindList L =
-                            gj_bind_list(G, P.bdir[j][b], tup[P.bpos[j][b] * FC + i], tup[P.bpos2[j][b] * FC + i]);
-                        keep = gj_bind_member(L, e);
+                        const uint32_t v = tup[P.bpos[j][b] * FC + i];
+                        keep = P.bdir[j][b] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
+                                            : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
                     }
                 }
                 cur += 32;
                 if (last) {
-                    const uint32_t gsz = (agg && keep) ? grp[i] : 1u;  // members of an aggregated group
+                    const uint32_t gsz = (EXT && agg && keep) ? grp[i] : 1u;  // members of an aggregated group
                     if (keep) {
                         for (uint32_t mbr = i; mbr < i + gsz; mbr++) {
                             uint64_t h = gj_mix64(hpre[mbr] ^ (uint64_t)e);
@@ -790,7 +822,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     if (DELTA)
                         cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
                                __popc(__ballot_sync(0xffffffffu, keep && sg < 0));
-                    else if (agg)
+                    else if (EXT && agg)
                         cnt += __reduce_add_sync(0xffffffffu, keep ? gsz : 0u);
                     else
                         cnt += __popc(__ballot_sync(0xffffffffu, keep));
@@ -801,7 +833,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     const uint32_t slot = nn + __popc(mask & lt);
                     for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
                     nt[j * FC + slot] = e;
-                    if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(j + 1))[slot] = sg;
+                    if (DELTA) reinterpret_cast<int8_t*>(ws + off_dsg(j + 1, EXT))[slot] = sg;
                 }
                 nn += __popc(mask);
                 if (lane == 0) stat_add(A.stats, 3, j + 1, __popc(mask));
@@ -824,7 +856,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             for (uint32_t i = lane; i < nn; i += 32) Bd.tup[c][i] = nt[c * FC + i];
                         if (DELTA)
                             for (uint32_t i = lane; i < nn; i += 32)
-                                Bd.sg[i] = reinterpret_cast<const int8_t*>(ws + off_dsg(j + 1))[i];
+                                Bd.sg[i] = reinterpret_cast<const int8_t*>(ws + off_dsg(j + 1, EXT))[i];
                         if (lane == 0) {
                             Bd.plan = (uint32_t)cur_q;
                             Bd.level = (uint32_t)(j + 1);
@@ -895,7 +927,61 @@ __global__ void k_seed_ranges(const Plan* plans, uint32_t nq, GraphView G, uint3
 
 }  // namespace
 
-int gj_fused_smem_bytes(uint32_t kmax) { return (int)(warp_bytes(kmax) * FW); }
+namespace {
+
+// Launch settings of one fused launch: dynamic shared memory, resident
+// blocks per SM (the context's cap applied) and the kernel variant.
+struct FusedCfg {
+    int smem = 0;
+    int per_sm = 1;
+    bool ext = false;
+};
+
+template <bool DELTA, bool EXT>
+int fused_cfg_t(gj_ctx* ctx, uint32_t kmax, bool cap, FusedCfg* c) {
+    c->smem = (int)(warp_bytes(kmax, DELTA, EXT) * FW);
+    if (c->smem > 48 * 1024)  // a per-device attribute: set on every call, as the context's device is current
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<DELTA, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              c->smem));
+    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, k_fused<DELTA, EXT>, FW * 32, c->smem));
+    if (cap && ctx->blocks_per_sm && (int)ctx->blocks_per_sm < c->per_sm) c->per_sm = (int)ctx->blocks_per_sm;
+    if (c->per_sm < 1) c->per_sm = 1;
+    c->ext = EXT;
+    return GJ_OK;
+}
+
+// The variant for plans[0..n): the extended one if any plan needs it.
+template <bool DELTA>
+int fused_cfg(gj_ctx* ctx, uint32_t kmax, const Plan* plans, uint32_t n, FusedCfg* c) {
+    bool ext = false;
+    for (uint32_t q = 0; q < n; q++) ext = ext || gj_plan_ext(plans[q]);
+    return ext ? fused_cfg_t<DELTA, true>(ctx, kmax, true, c) : fused_cfg_t<DELTA, false>(ctx, kmax, true, c);
+}
+
+// With donation on, warps wait for one another at the end of the launch,
+// so every block must be resident at once: a cooperative launch guarantees
+// that (the grid is sized from the occupancy of an idle GPU).
+template <bool DELTA, bool EXT>
+int launch_t(gj_ctx* ctx, FusedArgs& A, unsigned grid, int smem, cudaStream_t st) {
+    if (A.Q.b) {
+        void* args[] = {&A};
+        GJ_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_fused<DELTA, EXT>, dim3(grid), dim3(FW * 32), args,
+                                                     (size_t)smem, st));
+    } else {
+        k_fused<DELTA, EXT><<<grid, FW * 32, smem, st>>>(A);
+        GJ_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    GJ_LAUNCHED(ctx);
+    return GJ_OK;
+}
+
+template <bool DELTA>
+int launch_fused(gj_ctx* ctx, FusedArgs& A, const FusedCfg& c, cudaStream_t st) {
+    const unsigned grid = (unsigned)(ctx->sm_count * c.per_sm);
+    return c.ext ? launch_t<DELTA, true>(ctx, A, grid, c.smem, st) : launch_t<DELTA, false>(ctx, A, grid, c.smem, st);
+}
+
+}  // namespace
 
 constexpr uint32_t DONATION_CAP = 16384;  // ring slots (power of two)
 
@@ -926,23 +1012,6 @@ static int donation_queue(gj_ctx* ctx, unsigned int nwarps, DonationQueue* Q) {
     return GJ_OK;
 }
 
-// With donation on, warps wait for one another at the end of the launch,
-// so every block must be resident at once: a cooperative launch guarantees
-// that (the grid is sized from the occupancy of an idle GPU).
-template <bool DELTA>
-static int launch_fused(gj_ctx* ctx, FusedArgs& A, unsigned grid, int smem, cudaStream_t st) {
-    if (A.Q.b) {
-        void* args[] = {&A};
-        GJ_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_fused<DELTA>, dim3(grid), dim3(FW * 32), args,
-                                                     (size_t)smem, st));
-    } else {
-        k_fused<DELTA><<<grid, FW * 32, smem, st>>>(A);
-        GJ_CUDA_TRY(ctx, cudaGetLastError());
-    }
-    GJ_LAUNCHED(ctx);
-    return GJ_OK;
-}
-
 static int donation_check(gj_ctx* ctx, const DonationQueue& Q) {
     if (!Q.b) return GJ_OK;
     unsigned int err = 0;
@@ -954,20 +1023,14 @@ static int donation_check(gj_ctx* ctx, const DonationQueue& Q) {
     return GJ_OK;
 }
 
-int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax) {
-    const int smem = gj_fused_smem_bytes(kmax);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) {
+int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax, bool ext) {
+    FusedCfg c;
+    const int rc = ext ? fused_cfg_t<false, true>(ctx, kmax, false, &c) : fused_cfg_t<false, false>(ctx, kmax, false, &c);
+    if (rc != GJ_OK) {
         cudaGetLastError();
         return 1;
     }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    (void)ctx;
-    return per_sm < 1 ? 1 : per_sm;
+    return c.per_sm;
 }
 
 size_t gj_fused_async_bytes(uint32_t nq) {
@@ -997,18 +1060,11 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
-    const int smem = gj_fused_smem_bytes(kmax);
-    if (smem > 48 * 1024)
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
-    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
-    if (per_sm < 1) per_sm = 1;
+    FusedCfg cfg;
+    GJ_TRY(fused_cfg<false>(ctx, kmax, hp, nq, &cfg));
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     A.chunk = ctx->seed_chunk;
-    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
-    GJ_LAUNCHED(ctx);
-    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     *results = counts_d;
     return GJ_OK;
 }
@@ -1042,19 +1098,14 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
 
-    const int smem = gj_fused_smem_bytes(kmax);
-    if (smem > 48 * 1024)  // a per-device attribute: set on every call, as the context's device is current
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
-    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
-    if (per_sm < 1) per_sm = 1;
+    FusedCfg cfg;
+    GJ_TRY(fused_cfg<false>(ctx, kmax, hp.data(), nq, &cfg));
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     A.chunk = ctx->seed_chunk;
-    const unsigned grid = (unsigned)(ctx->sm_count * per_sm);
+    const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
     GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
     gj_timer_begin(ctx);
-    GJ_TRY(launch_fused<false>(ctx, A, grid, smem, st));
+    GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     gj_timer_end(ctx);
     std::vector<unsigned long long> h(2 * (size_t)nq + 1 + 45);
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), counts_d, 8 * h.size(), cudaMemcpyDeviceToHost, st));
@@ -1164,18 +1215,13 @@ int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uin
     GraphView G = g->view();
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, g->n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
-    const int smem = gj_fused_smem_bytes(kmax);
-    if (smem > 48 * 1024)
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<false>, FW * 32, smem));
-    if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
-    if (per_sm < 1) per_sm = 1;
+    std::vector<Plan> hp(nq);
+    for (uint32_t q = 0; q < nq; q++) hp[q] = qs[q]->plan;
+    FusedCfg cfg;
+    GJ_TRY(fused_cfg<false>(ctx, kmax, hp.data(), nq, &cfg));
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
     A.chunk = ctx->seed_chunk;
-    k_fused<false><<<(unsigned)(ctx->sm_count * per_sm), FW * 32, smem, st>>>(A);
-    GJ_LAUNCHED(ctx);
-    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     static_assert(sizeof(int64_t) == sizeof(unsigned long long), "count width");
     unsigned long long hs[45];
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(counts, counts_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
@@ -1252,21 +1298,16 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + 45), st));
         k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n, ctx->seed_chunk);
         GJ_LAUNCHED(ctx);
-        const int smem = (int)(warp_bytes(kmax, true) * FW);
-        if (smem > 48 * 1024)
-            GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        int per_sm = 0;
-        GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused<true>, FW * 32, smem));
-        if (per_sm < 1) per_sm = 1;
-        if (ctx->blocks_per_sm && (int)ctx->blocks_per_sm < per_sm) per_sm = (int)ctx->blocks_per_sm;
+        FusedCfg cfg;
+        GJ_TRY(fused_cfg<true>(ctx, kmax, plans + c0, nc, &cfg));
         FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
         A.chunk = ctx->seed_chunk;
         A.D = batch.view;
         A.B = batch;
-        const unsigned grid = (unsigned)(ctx->sm_count * per_sm);
+        const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
         GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
         gj_timer_begin(ctx);
-        GJ_TRY(launch_fused<true>(ctx, A, grid, smem, st));
+        GJ_TRY(launch_fused<true>(ctx, A, cfg, st));
         gj_timer_end(ctx);
         unsigned long long h[2 * 64 + 1 + 45];
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h, counts_d, 8 * (2 * (size_t)nc + 1 + 45), cudaMemcpyDeviceToHost, st));

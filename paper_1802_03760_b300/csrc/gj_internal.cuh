@@ -73,14 +73,18 @@ struct GraphView {
     const uint32_t* __restrict__ rt;
     const int64_t* __restrict__ to;   // triangle lists per forward slot (null until built)
     const uint32_t* __restrict__ tn;
+    const int64_t* __restrict__ tto;  // their hash sets
+    const uint32_t* __restrict__ tt;
 };
 
 // The ternary relation tri(a, b, c) (a -> b, a -> c, b -> c; Section 5.4)
 // indexed by its first two attributes: for the forward slot e of the edge
 // a -> b, the c are nbr[off[e] .. off[e+1]), ascending.
 struct gj_tri {
-    int64_t* off = nullptr;  // [m + 1]
-    uint32_t* nbr = nullptr; // [count]
+    int64_t* off = nullptr;      // [m + 1]
+    uint32_t* nbr = nullptr;     // [count]
+    int64_t* tab_off = nullptr;  // [m + 1] hash sets of the lists of at least GJ_HASH_MIN_DEG entries
+    uint32_t* tab = nullptr;
     uint64_t count = 0;
 };
 
@@ -97,7 +101,7 @@ struct gj_graph {
     uint32_t load_flags = 0;
     GraphView view() const {
         return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
-                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr};
+                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr, tri.tab_off, tri.tab};
     }
 };
 
@@ -105,7 +109,8 @@ struct gj_graph {
 
 // Execution plan of one query. Positions are places in the execution
 // (global attribute) order; x[p] is the value bound at position p.
-constexpr uint32_t GJ_MAX_LT = 8;  // inequality filters per level
+constexpr uint32_t GJ_MAX_LT = 8;     // inequality filters per level
+constexpr uint32_t GJ_MAX_BIND = 12;  // relations binding one level
 enum { GJ_BIND_FWD = 0, GJ_BIND_REV = 1, GJ_BIND_TRI = 2 };
 struct Plan {
     uint32_t k;
@@ -127,13 +132,13 @@ struct Plan {
     // x_bpos)), or the triangle list of the edge x[bpos] -> x[bpos2]
     // (GJ_BIND_TRI: atom tri(x_bpos, x_bpos2, x_p), Section 5.4).
     uint32_t nb[GJ_MAX_K];
-    uint8_t bpos[GJ_MAX_K][GJ_MAX_ATOMS];
-    uint8_t bpos2[GJ_MAX_K][GJ_MAX_ATOMS];
-    uint8_t bdir[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t bpos[GJ_MAX_K][GJ_MAX_BIND];
+    uint8_t bpos2[GJ_MAX_K][GJ_MAX_BIND];
+    uint8_t bdir[GJ_MAX_K][GJ_MAX_BIND];
     // Delta queries (Section 3.3.1): which version each atom reads, 0 = the
     // committed graph (old), 1 = the committed graph plus the batch (new).
     // Static plans leave these 0.
-    uint8_t bview[GJ_MAX_K][GJ_MAX_ATOMS];
+    uint8_t bview[GJ_MAX_K][GJ_MAX_BIND];
     uint8_t sf_view[GJ_MAX_ATOMS];
     // Inequality filters (Section 5.4) of level p: the new value x_p must be
     // below (lt_less 1) or above (0) x[lt_pos]. Level 1 holds the filters
@@ -307,10 +312,13 @@ int gj_delta_eval(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const
 // One launch over nq queries; counts/checksums are host arrays of nq.
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums);
-int gj_fused_smem_bytes(uint32_t kmax);
 size_t gj_fused_async_bytes(uint32_t nq);
-// Resident blocks per SM of the static fused kernel for queries of up to kmax attributes.
-int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax);
+// Resident blocks per SM of the static fused kernel for queries of up to kmax
+// attributes (ext: the variant for tri atoms, inequalities or aggregation).
+int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax, bool ext);
+// Whether a plan needs the fused kernel's extended variant (tri atoms,
+// inequality filters or an aggregated last level).
+bool gj_plan_ext(const Plan& p);
 int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t nq, cudaStream_t st, void* dscratch,
                      unsigned long long** results);
 
@@ -505,7 +513,9 @@ __device__ __forceinline__ BindList gj_bind_list(const GraphView& G, uint32_t di
         const int64_t e = gj_find(G.fn + s, (uint32_t)(__ldg(G.fo + v + 1) - s), v2);
         if (e < 0) return BindList{G.fn, 0u, nullptr, 0u};
         const int64_t a = __ldg(G.to + s + e);
-        return BindList{G.tn + a, (uint32_t)(__ldg(G.to + s + e + 1) - a), nullptr, 0u};
+        const uint32_t len = (uint32_t)(__ldg(G.to + s + e + 1) - a);
+        if (len >= GJ_HASH_MIN_DEG) return BindList{G.tn + a, len, G.tt + __ldg(G.tto + s + e), gj_tab_bits(len)};
+        return BindList{G.tn + a, len, nullptr, 0u};
     }
     const int64_t* off = dir ? G.ro : G.fo;
     const int64_t s = __ldg(off + v);

@@ -45,6 +45,16 @@ uint32_t last_level_reads(const Plan* p) {
 
 }  // namespace
 
+bool gj_plan_ext(const Plan& p) {
+    if (p.agg) return true;
+    for (uint32_t j = 1; j < p.k; j++) {
+        if (p.nlt[j]) return true;
+        for (uint32_t b = 0; j >= 2 && b < p.nb[j]; b++)
+            if (p.bdir[j][b] == GJ_BIND_TRI) return true;
+    }
+    return false;
+}
+
 int gj_plan_compile(const gj_query* q, Plan* p, std::string* why) {
     auto bad = [&](const char* m) {
         if (why) *why = m;
@@ -118,14 +128,14 @@ int gj_plan_compile(const gj_query* q, Plan* p, std::string* why) {
             if (pd == j && ps < j) { dir = GJ_BIND_FWD; bp = ps; }       // E(x_ps, x_j): out-neighbours of x_ps
             else if (ps == j && pd < j) { dir = GJ_BIND_REV; bp = pd; }  // E(x_j, x_pd): in-neighbours of x_pd
             if (dir < 0) continue;
-            if (nb >= GJ_MAX_ATOMS) return bad("more than 16 relations bind one attribute");
+            if (nb >= GJ_MAX_BIND) return bad("more than 12 relations bind one attribute");
             p->bpos[j][nb] = (uint8_t)bp;
             p->bdir[j][nb] = (uint8_t)dir;
             nb++;
         }
         for (uint32_t t = 0; t < ntri; t++) {
             if (p->qpos[q->tc[t]] != j) continue;
-            if (nb >= GJ_MAX_ATOMS) return bad("more than 16 relations bind one attribute");
+            if (nb >= GJ_MAX_BIND) return bad("more than 12 relations bind one attribute");
             p->bpos[j][nb] = (uint8_t)p->qpos[q->ta[t]];
             p->bpos2[j][nb] = (uint8_t)p->qpos[q->tb[t]];
             p->bdir[j][nb] = GJ_BIND_TRI;
@@ -135,9 +145,14 @@ int gj_plan_compile(const gj_query* q, Plan* p, std::string* why) {
         p->nb[j] = nb;
         if (!add_filters(q, p, j, why)) return GJ_E_INVALID;
     }
+    // Aggregation pays when the positions the last level does not read are
+    // the most recently bound ones (a suffix k-1-s .. k-2 of the order): the
+    // prefixes of a batch that share a parent then agree on everything the
+    // last level reads and sit next to one another.
     if (k >= 3) {
-        const uint32_t reads = last_level_reads(p);
-        p->agg = (reads != (1u << (k - 1)) - 1) ? reads : 0u;
+        const uint32_t all = (1u << (k - 1)) - 1, reads = last_level_reads(p), skip = all & ~reads;
+        const bool suffix = skip && ((skip + (skip & (0u - skip))) & all) == 0;  // one run of bits ending at k-2
+        p->agg = suffix ? reads : 0u;
     }
     return GJ_OK;
 }
@@ -210,6 +225,7 @@ int gj_plan_compile_delta(const gj_query* q, uint32_t i, Plan* p, std::string* w
             if (dir < 0) continue;
             p->bpos[j][nb] = (uint8_t)bp;
             p->bdir[j][nb] = (uint8_t)dir;
+            if (nb >= GJ_MAX_BIND) return bad("more than 12 relations bind one attribute");
             p->bview[j][nb] = (uint8_t)(t < i ? GJ_VIEW_NEW : GJ_VIEW_OLD);
             nb++;
         }

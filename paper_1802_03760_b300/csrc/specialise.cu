@@ -130,12 +130,71 @@ __global__ void __launch_bounds__(TW * 32) k_tri_lists(GraphView G, uint64_t m, 
     }
 }
 
+// Slot count of each triangle list's hash set (0 for lists shorter than GJ_HASH_MIN_DEG).
+__global__ void k_tri_tab_sizes(const int64_t* __restrict__ toff, uint64_t m, int64_t* __restrict__ size) {
+    GRID_STRIDE(e, m) {
+        const uint32_t len = (uint32_t)(toff[e + 1] - toff[e]);
+        size[e] = len >= GJ_HASH_MIN_DEG ? (int64_t)(1ll << gj_tab_bits(len)) : 0;
+    }
+}
+
+// Fills the hash sets of the long triangle lists, one warp per list (the
+// same layout and probing as the index's sets: linear probing from the first
+// slot of the key's home group of eight).
+__global__ void k_tri_tab_insert(const int64_t* __restrict__ toff, const uint32_t* __restrict__ tn, uint64_t m,
+                                 const int64_t* __restrict__ tab_off, uint32_t* __restrict__ tab) {
+    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (uint64_t e = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); e < m; e += warps) {
+        const int64_t a = toff[e];
+        const uint32_t len = (uint32_t)(toff[e + 1] - a);
+        if (len < GJ_HASH_MIN_DEG) continue;
+        const uint32_t bits = gj_tab_bits(len), mask = (1u << bits) - 1u;
+        uint32_t* t = tab + tab_off[e];
+        for (uint32_t i = lane; i < len; i += 32) {
+            const uint32_t x = tn[a + i];
+            uint32_t h = gj_tab_start(x, bits);
+            for (uint32_t probe = 0; probe <= mask; probe++) {
+                if (atomicCAS(t + h, GJ_EMPTY, x) == GJ_EMPTY) break;
+                h = (h + 1u) & mask;
+            }
+        }
+    }
+}
+
 }  // namespace
 
 void gj_tri_release(gj_tri& t) {
-    if (t.off) cudaFree(t.off);
-    if (t.nbr) cudaFree(t.nbr);
+    for (void* p : {(void*)t.off, (void*)t.nbr, (void*)t.tab_off, (void*)t.tab})
+        if (p) cudaFree(p);
     t = gj_tri{};
+}
+
+// Hash sets of t's long lists (after its lists are written).
+static int tri_tables(gj_ctx* ctx, uint64_t m, gj_tri& t) {
+    cudaStream_t st = ctx->stream;
+    GJ_CUDA_TRY(ctx, cudaMalloc(&t.tab_off, sizeof(int64_t) * (m + 1)));
+    int64_t* size = nullptr;
+    GJ_CUDA_TRY(ctx, cudaMallocAsync(&size, sizeof(int64_t) * (m ? m : 1), st));
+    if (m) {
+        k_tri_tab_sizes<<<grid_for(ctx, m), 256, 0, st>>>(t.off, m, size);
+        GJ_LAUNCHED(ctx);
+    }
+    int rc = gj_scan_i64(ctx, size, t.tab_off, m);
+    int64_t tsz = 0;
+    if (rc == GJ_OK && (cudaMemcpyAsync(&tsz, t.tab_off + m, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaStreamSynchronize(st) != cudaSuccess))
+        rc = GJ_E_CUDA;
+    cudaFreeAsync(size, st);
+    GJ_TRY(rc);
+    GJ_CUDA_TRY(ctx, cudaMalloc(&t.tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
+    if (tsz > 0) {
+        GJ_CUDA_TRY(ctx, cudaMemsetAsync(t.tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
+        k_tri_tab_insert<<<(unsigned)ctx->sm_count * 8, 256, 0, st>>>(t.off, t.nbr, m, t.tab_off, t.tab);
+        GJ_LAUNCHED(ctx);
+    }
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    return GJ_OK;
 }
 
 int gj_tri_build(gj_ctx* ctx, gj_graph* g) {
@@ -178,6 +237,7 @@ int gj_tri_build(gj_ctx* ctx, gj_graph* g) {
     }
     if (rc == GJ_OK) rc = run(1);
     cudaFreeAsync(cnt, st);
+    if (rc == GJ_OK) rc = tri_tables(ctx, m, t);
     if (rc == GJ_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GJ_E_CUDA;
     if (rc != GJ_OK) {
         gj_tri_release(t);
