@@ -45,7 +45,7 @@ def test_reference_arm_prints_one_line(monkeypatch):
     assert line["value"] >= 0 and line["config"]["workload"] == bench.workload_name(10, bench.BENCH_QUERIES)
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
-    assert "first attribute in [0, " in cb["sample"]
+    assert "ranges of 64 vertex ids at seeded random offsets" in cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "matches/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
@@ -81,3 +81,27 @@ def test_algorithmic_bytes_4clique_on_complete_dag():
     level2 = 4 * 2 * 15 + 16 * 30 + 4 * 20 + 4 * 20 * 1 + 4 * 3 * 20
     level3 = 4 * 3 * 20 + 16 * 60 + 4 * 15 + 4 * 15 * 2
     assert bench.algorithmic_bytes(w, 4) == 8 * 15 + level2 + level3 == 2500
+
+
+def test_golden_bytes_follow_the_cost_model():
+    """The roofline's algorithmic bytes at full size come from the oracle's
+    work units in the committed golden: for the triangle, 8 bytes per seed
+    edge and, per seed, 4*2 + 16*2 + 4c + 4c bytes (two binding lists)."""
+    gold = bench.golden_static(20)
+    assert gold is not None and gold["edges"] == 16084904
+    st = gold["queries"]["triangle"]["stats"]
+    m, c = gold["edges"], st["proposals"][2]
+    assert st["extended"][2] == m and st["nbind_sum"][2] == 2 * m
+    assert bench.oracle_bytes(gold, "triangle") == 8 * m + 8 * m + 16 * 2 * m + 4 * c + 4 * c
+    assert bench.golden_static(20, seed=2) is None and bench.golden_static(7) is None
+
+
+def test_traffic_only_from_a_capture_of_the_current_kernel(tmp_path, monkeypatch):
+    sha = bench.kernel_sources_sha()
+    f = tmp_path / "p.md"
+    monkeypatch.setattr(bench, "PROFILE", str(f))
+    assert bench.profiled_traffic()[0] is None
+    f.write_text("kernel_sources_sha256: %s\ntraffic_bytes_per_launch: 1234\n" % sha)
+    assert bench.profiled_traffic()[0] == 1234
+    f.write_text("kernel_sources_sha256: %s\ntraffic_bytes_per_launch: 1234\n" % ("0" * 64))
+    assert bench.profiled_traffic() == (None, "kernel changed since the ncu capture")
