@@ -578,7 +578,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA, EXT));
             const uint8_t* grp = ws + off_grp(j, DELTA, EXT);
             const bool agg = EXT && !DELTA && last && P.agg;
-            constexpr int MAXO = 3;  // other binding lists cached for a step-uniform prefix
+            // other binding lists cached in registers for a step-uniform prefix:
+            // two for plain edge queries (up to 4-cliques), one in the extended
+            // variant (its code size and registers cost more than the cache saves)
+            constexpr int MAXO = EXT ? 1 : 2;
             const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
             uint32_t ol[MAXO], obits[MAXO];
             uint32_t cached = 0xffffffffu;

@@ -75,6 +75,8 @@ struct GraphView {
     const uint32_t* __restrict__ tn;
     const int64_t* __restrict__ tto;  // their hash sets
     const uint32_t* __restrict__ tt;
+    const uint4* __restrict__ em;     // edge (a, b) -> its forward slot: {a, b, slot, 0}, 2^ebits entries
+    uint32_t ebits;
 };
 
 // The ternary relation tri(a, b, c) (a -> b, a -> c, b -> c; Section 5.4)
@@ -85,6 +87,10 @@ struct gj_tri {
     uint32_t* nbr = nullptr;     // [count]
     int64_t* tab_off = nullptr;  // [m + 1] hash sets of the lists of at least GJ_HASH_MIN_DEG entries
     uint32_t* tab = nullptr;
+    // open-addressing map from an edge (a, b) to its forward slot, so that the
+    // list of a tri atom is found with one probe instead of a search of out(a)
+    uint4* emap = nullptr;
+    uint32_t ebits = 0;
     uint64_t count = 0;
 };
 
@@ -101,7 +107,8 @@ struct gj_graph {
     uint32_t load_flags = 0;
     GraphView view() const {
         return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
-                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr, tri.tab_off, tri.tab};
+                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr, tri.tab_off, tri.tab,
+                         tri.emap, tri.ebits};
     }
 };
 
@@ -483,19 +490,6 @@ __device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaVi
     return dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
 }
 
-// Position of e in the sorted list a[0, len), or -1: branch-free binary
-// search over power-of-two steps.
-__device__ __forceinline__ int64_t gj_find(const uint32_t* __restrict__ a, uint32_t len, uint32_t e) {
-    if (len == 0) return -1;
-    uint32_t step = 1u << (31 - __clz(len));
-    uint32_t pos = (__ldg(a + (len - step)) <= e) ? len - step : 0u;
-    for (step >>= 1; step; step >>= 1) {
-        const uint32_t q = pos + step;
-        pos = (__ldg(a + q) <= e) ? q : pos;
-    }
-    return __ldg(a + pos) == e ? (int64_t)pos : -1;
-}
-
 // The list a binding of a plan level reads for one prefix (static plans):
 // the sorted list p[0, len) and, for long index lists, its hash set (bits
 // > 0). v is x[bpos]; v2 is x[bpos2] (tri bindings only).
@@ -506,15 +500,33 @@ struct BindList {
     uint32_t bits;
 };
 
+// Home entry of the edge (a, b) in the edge map: multiplicative hashing of
+// the 64-bit pair with the 64-bit golden-ratio constant (Knuth, TAOCP vol. 3,
+// Section 6.4).
+__host__ __device__ __forceinline__ uint32_t gj_edge_home(uint32_t a, uint32_t b, uint32_t bits) {
+    return (uint32_t)(((((uint64_t)a << 32) | b) * 0x9e3779b97f4a7c15ULL) >> (64 - bits));
+}
+
+// Forward slot of the edge a -> b, or -1 (edge map lookup, linear probing).
+__device__ __forceinline__ int64_t gj_edge_slot(const GraphView& G, uint32_t a, uint32_t b) {
+    const uint32_t mask = (uint32_t)((1ull << G.ebits) - 1u);
+    uint32_t h = gj_edge_home(a, b, G.ebits);
+    while (true) {
+        const uint4 E = __ldg(G.em + h);
+        if (E.x == a && E.y == b) return (int64_t)E.z;
+        if (E.x == GJ_EMPTY) return -1;
+        h = (h + 1u) & mask;
+    }
+}
+
 __device__ __forceinline__ BindList gj_bind_list(const GraphView& G, uint32_t dir, uint32_t v, uint32_t v2) {
     if (dir == GJ_BIND_TRI) {
-        // the triangles on the edge v -> v2: find its forward slot, then its list
-        const int64_t s = __ldg(G.fo + v);
-        const int64_t e = gj_find(G.fn + s, (uint32_t)(__ldg(G.fo + v + 1) - s), v2);
+        // the triangles on the edge v -> v2: its forward slot, then its list
+        const int64_t e = gj_edge_slot(G, v, v2);
         if (e < 0) return BindList{G.fn, 0u, nullptr, 0u};
-        const int64_t a = __ldg(G.to + s + e);
-        const uint32_t len = (uint32_t)(__ldg(G.to + s + e + 1) - a);
-        if (len >= GJ_HASH_MIN_DEG) return BindList{G.tn + a, len, G.tt + __ldg(G.tto + s + e), gj_tab_bits(len)};
+        const int64_t a = __ldg(G.to + e);
+        const uint32_t len = (uint32_t)(__ldg(G.to + e + 1) - a);
+        if (len >= GJ_HASH_MIN_DEG) return BindList{G.tn + a, len, G.tt + __ldg(G.tto + e), gj_tab_bits(len)};
         return BindList{G.tn + a, len, nullptr, 0u};
     }
     const int64_t* off = dir ? G.ro : G.fo;

@@ -162,12 +162,47 @@ __global__ void k_tri_tab_insert(const int64_t* __restrict__ toff, const uint32_
     }
 }
 
+// Inserts every forward edge (key[e], nbr[e]) with its slot e into the edge
+// map (linear probing; the map has at least twice as many entries as edges).
+__global__ void k_edge_map(const uint32_t* __restrict__ key, const uint32_t* __restrict__ nbr, uint64_t m,
+                           uint4* __restrict__ em, uint32_t bits) {
+    const uint32_t mask = (uint32_t)((1ull << bits) - 1u);
+    GRID_STRIDE(e, m) {
+        const uint32_t a = key[e], b = nbr[e];
+        const unsigned long long want = ((unsigned long long)b << 32) | a;  // {x = a, y = b} in memory order
+        uint32_t h = gj_edge_home(a, b, bits);
+        for (uint64_t probe = 0; probe <= mask; probe++) {
+            unsigned long long* w = reinterpret_cast<unsigned long long*>(em + h);
+            if (atomicCAS(w, ~0ull, want) == ~0ull) {
+                em[h].z = (uint32_t)e;
+                break;
+            }
+            h = (h + 1u) & mask;
+        }
+    }
+}
+
 }  // namespace
 
 void gj_tri_release(gj_tri& t) {
-    for (void* p : {(void*)t.off, (void*)t.nbr, (void*)t.tab_off, (void*)t.tab})
+    for (void* p : {(void*)t.off, (void*)t.nbr, (void*)t.tab_off, (void*)t.tab, (void*)t.emap})
         if (p) cudaFree(p);
     t = gj_tri{};
+}
+
+// The edge map of the forward index (2^ceil(log2(2 m)) entries, at least 2).
+static int edge_map(gj_ctx* ctx, const gj_graph* g, gj_tri& t) {
+    uint32_t bits = 1;
+    while ((1ull << bits) < 2 * g->m) bits++;
+    GJ_CUDA_TRY(ctx, cudaMalloc(&t.emap, sizeof(uint4) << bits));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(t.emap, 0xff, sizeof(uint4) << bits, ctx->stream));
+    if (g->m) {
+        k_edge_map<<<grid_for(ctx, g->m), 256, 0, ctx->stream>>>(g->fwd.key, g->fwd.nbr, g->m, t.emap, bits);
+        GJ_LAUNCHED(ctx);
+    }
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
+    t.ebits = bits;
+    return GJ_OK;
 }
 
 // Hash sets of t's long lists (after its lists are written).
@@ -238,6 +273,7 @@ int gj_tri_build(gj_ctx* ctx, gj_graph* g) {
     if (rc == GJ_OK) rc = run(1);
     cudaFreeAsync(cnt, st);
     if (rc == GJ_OK) rc = tri_tables(ctx, m, t);
+    if (rc == GJ_OK) rc = edge_map(ctx, g, t);
     if (rc == GJ_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GJ_E_CUDA;
     if (rc != GJ_OK) {
         gj_tri_release(t);
