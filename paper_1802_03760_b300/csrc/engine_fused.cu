@@ -614,15 +614,25 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 cached = pi;
             };
             // hashes the nsv buffered matches against every member of the group
-            // that starts at prefix g0 (g members): count += nsv * g
+            // that starts at prefix g0 (g members): count += nsv * g. The g * nsv
+            // (member, match) pairs are dealt to the lanes in turn, so every lane
+            // hashes the same number of them.
             auto flush_group = [&](uint32_t g0, uint32_t g, uint32_t nsv) {
                 cnt += (unsigned long long)nsv * g;
-                for (uint32_t mbr = g0; mbr < g0 + g; mbr++) {
-                    const uint64_t hm = hpre[mbr];
-                    for (uint32_t t = lane; t < nsv; t += 32) {
-                        uint64_t h = gj_mix64(hm ^ (uint64_t)sv[t]);
-                        for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
-                        chk += h;
+                uint32_t mbr = g0, t = lane;  // pair lane + 32 i is (member, match) = (mbr, t)
+                while (t >= nsv) {
+                    t -= nsv;
+                    mbr++;
+                }
+                const uint32_t gend = g0 + g;
+                while (mbr < gend) {
+                    uint64_t h = gj_mix64(hpre[mbr] ^ (uint64_t)sv[t]);
+                    for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
+                    chk += h;
+                    t += 32;  // once nsv >= 32 (every flush but a group's last) at most one wrap
+                    while (t >= nsv) {
+                        t -= nsv;
+                        mbr++;
                     }
                 }
                 __syncwarp();
