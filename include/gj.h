@@ -55,7 +55,7 @@ enum {
     GJ_E_ADMIT = -4,      /* request needs more device memory than the budget allows */
     GJ_E_TRUNCATED = -5,  /* more matches than the output capacity */
     GJ_E_TIMEOUT = -6,    /* a bounded wait expired */
-    GJ_E_OVERFLOW = -7,   /* reserved, not returned: counts are exact below 2^63 and not checked for wrap-around */
+    GJ_E_OVERFLOW = -7,   /* a match count passed 2^63 - 1 (the int64 result would wrap) */
     GJ_E_CUDA = -8,       /* a CUDA runtime call failed (gj_last_error has the text) */
     GJ_E_PENDING = -9,    /* request not finished yet */
     GJ_E_NOTFOUND = -10   /* unknown request id */
@@ -268,13 +268,26 @@ typedef struct {
      * is idle (default), 1: whenever a queue slot is free (stress setting),
      * 2: off. Results never depend on it. */
     uint32_t donation;
+    /* The fused engine's end-of-launch wait (warps without work waiting for
+     * donations until every warp is idle) gives up with GJ_E_TIMEOUT once the
+     * donation queue has shown no progress for wait_ms milliseconds; 0 =
+     * 10000. Working warps interact with the queue at least every ~1000
+     * candidates, so the bound only ends waits that cannot end otherwise. */
+    uint32_t wait_ms;
+    /* Failure injection for tests; 0 = off. 1: the end-of-launch wait counts
+     * one more warp than the launch has, so it can only end by its time bound
+     * (the count call returns GJ_E_TIMEOUT; the context stays usable). 2: the
+     * fused engine's per-query counts start at 2^63 - 1024, so a query with
+     * more than 1023 matches returns GJ_E_OVERFLOW. */
+    uint32_t fault;
 } gj_tuning;
 /* Copies the context's current settings to *out (fused_ms and plain_ms are
  * 0: only gj_autotune's output carries them). Errors: GJ_E_INVALID (null pointer). */
 int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
 /* Replaces the context's settings (fused_ms and plain_ms are ignored); results
- * never depend on them. Errors: GJ_E_INVALID (seed_chunk out of range or not
- * a multiple of 32, budget under 1 MiB, donation > 2). */
+ * never depend on them (except for the failure-injection field). Errors:
+ * GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under
+ * 1 MiB, donation > 2, fault > 2). */
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
 /*
  * Chooses the context's launch settings by timing the given queries on the

@@ -435,14 +435,18 @@ int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out) {
     out->blocks_per_sm = ctx->blocks_per_sm;
     out->prefix_buffer_bytes = ctx->opt.prefix_buffer_bytes;
     out->donation = ctx->donation;
+    out->wait_ms = ctx->wait_ms;
+    out->fault = ctx->fault;
     return GJ_OK;
 }
 
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
     if (!ctx || !t || t->seed_chunk < 32 || t->seed_chunk > 4096 || t->seed_chunk % 32) return GJ_E_INVALID;
     if (t->prefix_buffer_bytes && t->prefix_buffer_bytes < (1ull << 20)) return GJ_E_INVALID;
-    if (t->donation > 2) return GJ_E_INVALID;
+    if (t->donation > 2 || t->fault > GJ_FAULT_COUNT) return GJ_E_INVALID;
     ctx->seed_chunk = t->seed_chunk;
+    ctx->wait_ms = t->wait_ms;
+    ctx->fault = t->fault;
     ctx->donation = t->donation;
     ctx->blocks_per_sm = t->blocks_per_sm;
     ctx->opt.prefix_buffer_bytes = t->prefix_buffer_bytes;

@@ -70,13 +70,23 @@ struct FusedArgs {
     unsigned long long* counts; // [nq]
     unsigned long long* chks;   // [nq]
     unsigned long long* stats;  // [5 * 9] extended, nbind, proposals, produced, seeds; may be null
+    unsigned long long* ovf;    // set when a static count passes 2^63 - 1 (may be null)
     DeltaView D;                // delta plans: the batch's per-direction insert/delete arrays
     DeltaBatch B;               // delta plans: the batch's signed changes (the seeds)
     uint32_t chunk = SEED_CHUNK;  // seeds a warp takes per grab (multiple of 32)
     DonationQueue Q;
+    uint64_t wait_ns = 0;       // bound of the end-of-launch wait without progress
 };
 
-constexpr uint32_t IDLE_WAIT_LIMIT = 1u << 26;  // iterations of the idle wait before giving up
+// Counter block of a launch after the per-query counts and checksums: the
+// shared work counter, the work units (5 x 9) and the overflow flag.
+constexpr size_t NSTAT = 5 * 9 + 1;
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Shared-memory layout of one warp (identical on host and device): the
 // plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), the
@@ -240,7 +250,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         unsigned long long h = chk;
         for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
         if (lane == 0 && cur_q >= 0) {
-            if (cnt) atomicAdd(A.counts + cur_q, cnt);
+            if (cnt) {
+                const unsigned long long old = atomicAdd(A.counts + cur_q, cnt);
+                // a static count is exact below 2^63 (it is reported as int64)
+                if (!DELTA && A.ovf && (old + cnt < old || ((old + cnt) >> 63))) atomicOr(A.ovf, 1ull);
+            }
             if (h) atomicAdd(A.chks + cur_q, h);
         }
         cnt = 0;
@@ -398,12 +412,17 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
                 if (!A.Q.b) break;
                 // No seeds left: take a donated bundle, or wait until every
-                // warp is idle and none is left (bounded wait).
+                // warp is idle and none is left. The wait is bounded: it gives
+                // up once the queue (head, tail, idle count) has not changed
+                // for A.wait_ns, or once another warp has given up.
                 const unsigned long long mask = A.Q.cap - 1;
                 long long took = -1;
                 bool idle_marked = false, give_up = false;
                 uint32_t backoff = 64;  // ns; doubles while nothing is published (less polling traffic)
-                for (uint32_t it = 0;; it++) {
+                unsigned long long seen_h = ~0ull, seen_t = ~0ull;
+                unsigned int seen_i = ~0u;
+                uint64_t since = globaltimer_ns();
+                while (true) {
                     long long b = -1;
                     if (lane == 0) {
                         const unsigned long long h = vload64(A.Q.head);
@@ -416,6 +435,19 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             idle_marked = true;
                             if (vload(A.Q.idle) == A.Q.nwarps && vload64(A.Q.head) == vload64(A.Q.tail)) b = -2;
                         }
+                        if (b == -1) {
+                            const unsigned long long t = vload64(A.Q.tail);
+                            const unsigned int iw = vload(A.Q.idle);
+                            const uint64_t now = globaltimer_ns();
+                            if (h != seen_h || t != seen_t || iw != seen_i) {
+                                seen_h = h;
+                                seen_t = t;
+                                seen_i = iw;
+                                since = now;
+                            } else if (now - since > A.wait_ns || vload(A.Q.err)) {
+                                b = -3;
+                            }
+                        }
                     }
                     b = __shfl_sync(0xffffffffu, b, 0);
                     idle_marked = __shfl_sync(0xffffffffu, idle_marked, 0);
@@ -424,7 +456,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         break;
                     }
                     if (b == -2) break;
-                    if (it >= IDLE_WAIT_LIMIT) {
+                    if (b == -3) {
                         give_up = true;
                         break;
                     }
@@ -1019,7 +1051,9 @@ static int donation_queue(gj_ctx* ctx, unsigned int nwarps, DonationQueue* Q) {
     Q->idle = (unsigned int*)(ctr + 64);
     Q->err = (unsigned int*)(ctr + 96);
     Q->seq = seq;
-    Q->nwarps = nwarps;
+    // failure injection for tests: the end-of-launch wait counts a warp that
+    // never arrives, so it can only end by its time bound (GJ_E_TIMEOUT)
+    Q->nwarps = nwarps + (ctx->fault == GJ_FAULT_WAIT ? 1u : 0u);
     Q->always = ctx->donation == 1 ? 1u : 0u;
     if (ctx->donation == 2) Q->b = nullptr;  // off
     return GJ_OK;
@@ -1070,13 +1104,14 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
     uint32_t kmax = 2;
     for (uint32_t q = 0; q < nq; q++) kmax = hp[q].k > kmax ? hp[q].k : kmax;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp, sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
-    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + NSTAT), st));
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
     FusedCfg cfg;
     GJ_TRY(fused_cfg<false>(ctx, kmax, hp, nq, &cfg));
-    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, stats + 45};
     A.chunk = ctx->seed_chunk;
+    A.wait_ns = gj_wait_ns(ctx);
     GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     *results = counts_d;
     return GJ_OK;
@@ -1106,27 +1141,36 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     std::vector<Plan> hp(nq);
     for (uint32_t q = 0; q < nq; q++) hp[q] = qs[q]->plan;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp.data(), sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
-    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + 45), st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + NSTAT), st));
     GraphView G = g->view();
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, v_lo, v_hi, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
+    // failure injection for tests: counts start just below 2^63
+    const uint64_t cbase = ctx->fault == GJ_FAULT_COUNT ? (1ull << 63) - 1024 : 0;
+    std::vector<unsigned long long> hbase(nq, cbase);
+    if (cbase) GJ_CUDA_TRY(ctx, cudaMemcpyAsync(counts_d, hbase.data(), 8 * (size_t)nq, cudaMemcpyHostToDevice, st));
 
     FusedCfg cfg;
     GJ_TRY(fused_cfg<false>(ctx, kmax, hp.data(), nq, &cfg));
-    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, stats + 45};
     A.chunk = ctx->seed_chunk;
+    A.wait_ns = gj_wait_ns(ctx);
     const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
     GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
     gj_timer_begin(ctx);
     GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     gj_timer_end(ctx);
-    std::vector<unsigned long long> h(2 * (size_t)nq + 1 + 45);
+    std::vector<unsigned long long> h(2 * (size_t)nq + 1 + NSTAT);
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), counts_d, 8 * h.size(), cudaMemcpyDeviceToHost, st));
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     GJ_TRY(donation_check(ctx, A.Q));
     GJ_TRY(gj_timer_collect(ctx));
+    if (h[2 * (size_t)nq + 1 + 45]) {
+        gj_set_error(ctx, GJ_E_OVERFLOW, "fused engine: a match count passed 2^63 - 1");
+        return GJ_E_OVERFLOW;
+    }
     for (uint32_t q = 0; q < nq; q++) {
-        counts[q] = (int64_t)h[q];
+        counts[q] = (int64_t)(h[q] - cbase);
         checksums[q] = h[nq + q];
     }
     gj_work_stats& W = ctx->work;
@@ -1166,7 +1210,7 @@ constexpr size_t NA_COUNTS = NA_QBASE + 8 * (NOALLOC_MAX_QUERIES + 1);    // zer
 constexpr size_t NA_CHKS = NA_COUNTS + 8 * NOALLOC_MAX_QUERIES;
 constexpr size_t NA_NEXT = NA_CHKS + 8 * NOALLOC_MAX_QUERIES;
 constexpr size_t NA_STATS = NA_NEXT + 8;
-constexpr size_t NA_END = NA_STATS + 8 * 45;
+constexpr size_t NA_END = NA_STATS + 8 * NSTAT;
 static_assert(NA_END <= NOALLOC_SCRATCH_BYTES, "no-allocation scratch too small");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -1232,15 +1276,25 @@ int count_noalloc(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uin
     for (uint32_t q = 0; q < nq; q++) hp[q] = qs[q]->plan;
     FusedCfg cfg;
     GJ_TRY(fused_cfg<false>(ctx, kmax, hp.data(), nq, &cfg));
-    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, stats + 45};
     A.chunk = ctx->seed_chunk;
+    A.wait_ns = gj_wait_ns(ctx);
     GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     static_assert(sizeof(int64_t) == sizeof(unsigned long long), "count width");
-    unsigned long long hs[45];
-    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(counts, counts_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
-    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(checksums, chks_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
+    unsigned long long hs[NSTAT];
+    std::vector<unsigned long long> hc(2 * (size_t)nq);
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data(), counts_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(hc.data() + nq, chks_d, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, st));
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (hs[45]) {
+        gj_set_error(ctx, GJ_E_OVERFLOW, "gj_count_noalloc: a match count passed 2^63 - 1");
+        return GJ_E_OVERFLOW;
+    }
+    for (uint32_t q = 0; q < nq; q++) {
+        counts[q] = (int64_t)hc[q];
+        checksums[q] = hc[nq + q];
+    }
     gj_work_stats& W = ctx->work;
     memset(&W, 0, sizeof(W));
     for (int j = 0; j < 9; j++) {
@@ -1308,13 +1362,14 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         uint32_t kmax = 2;
         for (uint32_t q = 0; q < nc; q++) kmax = plans[c0 + q].k > kmax ? plans[c0 + q].k : kmax;
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, plans + c0, sizeof(Plan) * nc, cudaMemcpyHostToDevice, st));
-        GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + 45), st));
+        GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + NSTAT), st));
         k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n, ctx->seed_chunk);
         GJ_LAUNCHED(ctx);
         FusedCfg cfg;
         GJ_TRY(fused_cfg<true>(ctx, kmax, plans + c0, nc, &cfg));
-        FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats};
+        FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, nullptr};
         A.chunk = ctx->seed_chunk;
+        A.wait_ns = gj_wait_ns(ctx);
         A.D = batch.view;
         A.B = batch;
         const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
@@ -1322,8 +1377,8 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         gj_timer_begin(ctx);
         GJ_TRY(launch_fused<true>(ctx, A, cfg, st));
         gj_timer_end(ctx);
-        unsigned long long h[2 * 64 + 1 + 45];
-        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h, counts_d, 8 * (2 * (size_t)nc + 1 + 45), cudaMemcpyDeviceToHost, st));
+        unsigned long long h[2 * 64 + 1 + NSTAT];
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(h, counts_d, 8 * (2 * (size_t)nc + 1 + NSTAT), cudaMemcpyDeviceToHost, st));
         GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
         GJ_TRY(donation_check(ctx, A.Q));
         for (uint32_t q = 0; q < nc; q++) {

@@ -244,7 +244,16 @@ struct gj_ctx {
     uint32_t seed_chunk = 32;    // fused engine: seeds per grab
     uint32_t blocks_per_sm = 0;  // fused engine: resident blocks per SM, 0 = as many as fit
     uint32_t donation = 0;       // fused engine work donation: 0 when warps idle, 1 always, 2 off
+    uint32_t wait_ms = 0;        // bound of the fused engine's end-of-launch wait without progress, 0 = 10 s
+    uint32_t fault = 0;          // failure injection for tests (GJ_FAULT_*)
 };
+
+// Failure injection (gj_tuning.fault): the fused engine's end-of-launch wait
+// misses one warp (it ends by its time bound), or its counts start just
+// below 2^63 (they overflow).
+enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2 };
+
+inline uint64_t gj_wait_ns(const gj_ctx* ctx) { return (uint64_t)(ctx->wait_ms ? ctx->wait_ms : 10000) * 1000000ull; }
 
 // Counts one kernel launch of ctx (gj_launch_count reports the total).
 #define GJ_LAUNCHED(ctx) ((ctx)->launches++)

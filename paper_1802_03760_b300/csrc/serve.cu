@@ -110,13 +110,15 @@ void reap(gj_server* S) {
                 const uint32_t nq = (uint32_t)r->qs.size();
                 r->counts.resize(nq);
                 r->chks.resize(nq);
+                bool ovf = false;
                 for (uint32_t k = 0; k < nq; k++) {
                     r->counts[k] = (int64_t)w->hres[o + k];
                     r->chks[k] = w->hres[w->nq + o + k];
+                    ovf = ovf || r->counts[k] < 0;  // a count past 2^63 - 1
                 }
                 o += nq;
                 r->version = w->version;
-                finish(S, r, st);
+                finish(S, r, (st == GJ_OK && ovf) ? GJ_E_OVERFLOW : st);
             }
             S->in_use -= w->mem;
         }

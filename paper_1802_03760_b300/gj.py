@@ -54,7 +54,7 @@ class WorkStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("seed_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("prefix_buffer_bytes", ctypes.c_uint64), ("fused_ms", ctypes.c_double), ("plain_ms", ctypes.c_double),
-                ("donation", ctypes.c_uint32)]
+                ("donation", ctypes.c_uint32), ("wait_ms", ctypes.c_uint32), ("fault", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -368,8 +368,8 @@ def get_tuning(ctx: Context) -> dict:
 
 
 def set_tuning(ctx: Context, seed_chunk: int = 32, blocks_per_sm: int = 0, prefix_buffer_bytes: int = 0,
-               donation: int = 0):
-    t = Tuning(seed_chunk, blocks_per_sm, prefix_buffer_bytes, 0.0, 0.0, donation)
+               donation: int = 0, wait_ms: int = 0, fault: int = 0):
+    t = Tuning(seed_chunk, blocks_per_sm, prefix_buffer_bytes, 0.0, 0.0, donation, wait_ms, fault)
     _check(lib().gj_set_tuning(ctx._h, ctypes.byref(t)), ctx)
 
 
