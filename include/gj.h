@@ -79,10 +79,12 @@ enum {
     GJ_ENGINE_FUSED = 1
 };
 
-/* Option flags. GJ_FLAG_DELTA_FUSED: evaluate the delta queries of update
- * batches with the fused engine instead of the level-synchronous one (the
- * default, which spreads a small batch's large fan-out over the whole GPU). */
-enum { GJ_FLAG_DELTA_FUSED = 1 };
+/* Option flags for the delta queries of update batches. By default a batch
+ * of fewer than 32768 normalised changes runs on the level-synchronous
+ * engine (which spreads a small batch's fan-out over the whole GPU at once)
+ * and a larger one on the fused engine (which balances its work by
+ * donation). GJ_FLAG_DELTA_FUSED / GJ_FLAG_DELTA_PLAIN force one of them. */
+enum { GJ_FLAG_DELTA_FUSED = 1, GJ_FLAG_DELTA_PLAIN = 2 };
 
 typedef struct {
     uint64_t prefix_buffer_bytes; /* cap on device prefix buffers of one evaluation; 0 = 512 MiB */

@@ -213,7 +213,7 @@ void gj_graph_free(gj_graph* g) {
     if (g->ctx->server) gj_serve_stop(g->ctx);  // the loop may still read g
     DevSet ds(g->ctx->device);
     cudaStreamSynchronize(g->ctx->stream);
-    for (gj_csr* c : {&g->fwd, &g->rev}) gj_csr_release(*c);
+    for (gj_csr* c : {&g->fwd, &g->rev, &g->spare_fwd, &g->spare_rev}) gj_csr_release(*c);
     gj_tri_release(g->tri);
     if (g->relabel) cudaFree(g->relabel);
     delete g;
@@ -573,7 +573,7 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
     std::vector<uint64_t> dh(nq);
     int rc = gj_delta_prepare(ctx, g, src, dst, sign, b, &buf);
     if (rc == GJ_OK) rc = gj_delta_eval(ctx, g, buf.batch, qs, nq,
-                                         (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN,
+                                         gj_delta_engine(ctx, buf.batch.n),
                                          dc.data(), dh.data());
     gj_work_stats sum = ctx->work;
     const uint64_t changes = buf.batch.n;

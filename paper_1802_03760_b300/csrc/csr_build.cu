@@ -132,6 +132,7 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->off, sizeof(int64_t) * ((size_t)n + 1)));
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->nbr, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->key, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
+    out->cap_m = (uint64_t)(mu ? mu : 1);
     if (m > 0) {
         k_scatter_unique<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag, pos, vb, out->nbr, out->key);
         GJ_LAUNCHED(ctx);
@@ -164,6 +165,7 @@ int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out) {
     cudaFreeAsync(size, st);
     GJ_TRY(rc);
     GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
+    out->cap_tab = (uint64_t)(tsz ? tsz : 1);
     if (tsz > 0) {
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(out->tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
         k_tab_insert<<<grid_for(ctx, mu), 256, 0, st>>>(out->off, out->nbr, out->key, mu, out->tab_off, out->tab);

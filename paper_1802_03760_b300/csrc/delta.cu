@@ -148,39 +148,198 @@ __global__ void k_range_map(const uint32_t* __restrict__ key, uint32_t n, int wh
     }
 }
 
-// flag[e] = 1 if index slot e (owner key[e], neighbour nbr[e]) survives the
-// batch's deletions in that direction.
-__global__ void k_keep_slots(const uint32_t* __restrict__ key, const uint32_t* __restrict__ nbr, uint64_t m,
-                             DeltaSide side, uint32_t* __restrict__ flag) {
-    GRID_STRIDE(e, m) {
-        const uint32_t u = key[e], v = nbr[e];
-        const uint4 r = gj_delta_ranges(side, u);
-        flag[e] = gj_contains(side.del_nbr + r.z, r.w - r.z, v) ? 0u : 1u;
+// Number of entries below x in the sorted list a[0, len).
+__device__ __forceinline__ uint64_t lower_count(const uint32_t* __restrict__ a, uint64_t len, uint32_t x) {
+    uint64_t lo = 0, hi = len;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// The list owners of the batch's inserts and deletes of one index
+// direction, as 64-bit keys (to be sorted and deduplicated).
+__global__ void k_touch_keys(const uint32_t* __restrict__ ik, uint32_t ni, const uint32_t* __restrict__ dk, uint32_t nd,
+                             uint64_t* __restrict__ keys) {
+    GRID_STRIDE(i, (uint64_t)ni + nd) keys[i] = i < ni ? ik[i] : dk[i - ni];
+}
+
+__global__ void k_run_flag(const uint64_t* __restrict__ keys, uint64_t n, uint32_t* __restrict__ flag) {
+    GRID_STRIDE(i, n) flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void k_run_compact(const uint64_t* __restrict__ keys, uint64_t n, const uint32_t* __restrict__ flag,
+                              const int64_t* __restrict__ pos, uint32_t* __restrict__ out) {
+    GRID_STRIDE(i, n) if (flag[i]) out[pos[i]] = (uint32_t)keys[i];
+}
+
+// Per touched vertex (ascending): the change of its list length and of its
+// hash set's slot count, its committed list length, its next list length and
+// its next hash set's slot count.
+__global__ void k_touch_info(const uint32_t* __restrict__ tv, uint32_t ntv, DeltaSide side,
+                             const int64_t* __restrict__ off, int64_t* __restrict__ dlen,
+                             int64_t* __restrict__ dtab, int64_t* __restrict__ olen, int64_t* __restrict__ nlen,
+                             int64_t* __restrict__ ntab) {
+    GRID_STRIDE(i, ntv) {
+        const uint32_t v = tv[i];
+        const uint4 r = gj_delta_ranges(side, v);
+        const int64_t d = (int64_t)(r.y - r.x) - (int64_t)(r.w - r.z);
+        const uint32_t ol = (uint32_t)(off[v + 1] - off[v]), nl = (uint32_t)((int64_t)ol + d);
+        const int64_t ot = ol >= GJ_HASH_MIN_DEG ? (1ll << gj_tab_bits(ol)) : 0;
+        const int64_t nt = nl >= GJ_HASH_MIN_DEG ? (1ll << gj_tab_bits(nl)) : 0;
+        dlen[i] = d;
+        dtab[i] = nt - ot;
+        olen[i] = ol;
+        nlen[i] = nl;
+        ntab[i] = nt;
     }
 }
 
-// Merges two (owner, neighbour)-sorted slot lists without common pairs: each
-// element's output position is its own index plus the number of elements of
-// the other list that sort before it.
-__global__ void k_merge_slots(const uint32_t* __restrict__ ak, const uint32_t* __restrict__ an, uint64_t na,
-                              const uint32_t* __restrict__ bk, const uint32_t* __restrict__ bn, uint64_t nb,
-                              uint32_t* __restrict__ ok, uint32_t* __restrict__ on) {
-    GRID_STRIDE(i, na + nb) {
-        const bool in_a = i < na;
-        const uint64_t j = in_a ? i : i - na;
-        const uint32_t k = in_a ? ak[j] : bk[j];
-        const uint32_t x = in_a ? an[j] : bn[j];
-        const uint64_t key = ((uint64_t)k << 32) | x;
-        const uint32_t* ok_ = in_a ? bk : ak;
-        const uint32_t* on_ = in_a ? bn : an;
-        uint64_t lo = 0, hi = in_a ? nb : na;
+// The touched vertex that owns flat item f, given the exclusive sums P of
+// the items per touched vertex: the last i with P[i] <= f.
+__device__ __forceinline__ uint32_t owner_of(const int64_t* __restrict__ P, uint32_t ntv, int64_t f) {
+    uint32_t lo = 0, hi = ntv;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (P[mid] <= f) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// The next version's offsets: every list and hash set moves by the sum of
+// the changes of the touched vertices before it (S, ST: exclusive sums).
+__global__ void k_shift_offsets(const int64_t* __restrict__ off, const int64_t* __restrict__ toff, uint32_t n,
+                                const uint32_t* __restrict__ tv, uint32_t ntv, const int64_t* __restrict__ S,
+                                const int64_t* __restrict__ ST, int64_t* __restrict__ noff,
+                                int64_t* __restrict__ ntoff) {
+    GRID_STRIDE(v, (uint64_t)n + 1) {
+        uint32_t lo = 0, hi = ntv;  // touched vertices below v
         while (lo < hi) {
-            const uint64_t mid = (lo + hi) >> 1;
-            const uint64_t mk = ((uint64_t)ok_[mid] << 32) | on_[mid];
-            if (mk < key) lo = mid + 1; else hi = mid;
+            const uint32_t mid = (lo + hi) >> 1;
+            if (tv[mid] < v) lo = mid + 1; else hi = mid;
         }
-        ok[j + lo] = k;
-        on[j + lo] = x;
+        noff[v] = off[v] + S[lo];
+        ntoff[v] = toff[v] + ST[lo];
+    }
+}
+
+// Block r moves the lists and hash sets of the untouched vertices between
+// touched vertices r - 1 and r to their new place (a constant shift).
+__global__ void k_shift_copy(const int64_t* __restrict__ off, const int64_t* __restrict__ toff,
+                             const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ key,
+                             const uint32_t* __restrict__ tab, uint32_t n, const uint32_t* __restrict__ tv, uint32_t ntv,
+                             const int64_t* __restrict__ S, const int64_t* __restrict__ ST, uint32_t* __restrict__ nnbr,
+                             uint32_t* __restrict__ nkey, uint32_t* __restrict__ ntab) {
+    for (uint64_t r = blockIdx.x; r <= ntv; r += gridDim.x) {
+        const uint32_t lo_v = r == 0 ? 0u : tv[r - 1] + 1, hi_v = r == ntv ? n : tv[r];
+        if (lo_v >= hi_v) continue;
+        // eight independent loads per thread before its stores (bytes in flight)
+        constexpr int U = 8;
+        const int64_t a = off[lo_v], b = off[hi_v], sh = S[r];
+        for (int64_t e0 = a + threadIdx.x; e0 < b; e0 += (int64_t)U * blockDim.x) {
+            uint32_t x[U], y[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                if (e < b) {
+                    x[u] = nbr[e];
+                    y[u] = key[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                if (e < b) {
+                    nnbr[e + sh] = x[u];
+                    nkey[e + sh] = y[u];
+                }
+            }
+        }
+        const int64_t ta = toff[lo_v], tb = toff[hi_v], tsh = ST[r];
+        for (int64_t e0 = ta + threadIdx.x; e0 < tb; e0 += (int64_t)U * blockDim.x) {
+            uint32_t x[U];
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                if (e < tb) x[u] = tab[e];
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t e = e0 + (int64_t)u * blockDim.x;
+                if (e < tb) ntab[e + tsh] = x[u];
+            }
+        }
+    }
+}
+
+// The next lists of the touched vertices: the committed entries that the
+// batch does not delete, and the batch's inserts, each written straight to
+// its place (all lists sorted; deletes are in the committed list, inserts are
+// not). Flat item f < OLP[ntv] is committed entry f - OLP[i] of touched vertex
+// i; item OLP[ntv] + e is insert e of the direction.
+__global__ void k_merge_touched(const int64_t* __restrict__ off, const uint32_t* __restrict__ nbr,
+                                const uint32_t* __restrict__ tv, uint32_t ntv, DeltaSide side,
+                                const int64_t* __restrict__ OLP, const int64_t* __restrict__ noff,
+                                uint32_t* __restrict__ nnbr, uint32_t* __restrict__ nkey) {
+    const int64_t nold = OLP[ntv];
+    GRID_STRIDE(f, (uint64_t)nold + side.nins) {
+        uint32_t v, x;
+        int64_t p;
+        if ((int64_t)f < nold) {
+            const uint32_t i = owner_of(OLP, ntv, (int64_t)f);
+            v = tv[i];
+            const uint4 r = gj_delta_ranges(side, v);
+            const int64_t t = (int64_t)f - OLP[i];
+            x = nbr[off[v] + t];
+            const uint32_t* del = side.del_nbr + r.z;
+            if (gj_contains(del, r.w - r.z, x)) continue;
+            // kept entries before x: t minus the deleted ones; plus the inserts below x
+            p = noff[v] + t - (int64_t)lower_count(del, r.w - r.z, x) +
+                (int64_t)lower_count(side.ins_nbr + r.x, r.y - r.x, x);
+        } else {
+            const uint32_t e = (uint32_t)((int64_t)f - nold);
+            v = side.ins_key[e];
+            x = side.ins_nbr[e];
+            const uint4 r = gj_delta_ranges(side, v);
+            const int64_t a = off[v], len = off[v + 1] - a;
+            p = noff[v] + (int64_t)(e - r.x) + (int64_t)lower_count(nbr + a, (uint64_t)len, x) -
+                (int64_t)lower_count(side.del_nbr + r.z, r.w - r.z, x);
+        }
+        nnbr[p] = x;
+        nkey[p] = v;
+    }
+}
+
+// Clears the next hash sets of the touched vertices (flat over their slots;
+// NTP: exclusive sums of their slot counts).
+__global__ void k_touched_clear(const uint32_t* __restrict__ tv, uint32_t ntv, const int64_t* __restrict__ NTP,
+                                const int64_t* __restrict__ ntoff, uint32_t* __restrict__ ntab) {
+    GRID_STRIDE(f, (uint64_t)NTP[ntv]) {
+        const uint32_t i = owner_of(NTP, ntv, (int64_t)f);
+        ntab[ntoff[tv[i]] + ((int64_t)f - NTP[i])] = GJ_EMPTY;
+    }
+}
+
+// Fills them from the next lists (flat over the list entries; NLP: exclusive
+// sums of the next list lengths), probing as gj_tab_member does: linearly
+// from the first slot of the key's home group.
+__global__ void k_touched_fill(const uint32_t* __restrict__ tv, uint32_t ntv, const int64_t* __restrict__ NLP,
+                               const int64_t* __restrict__ noff, const uint32_t* __restrict__ nnbr,
+                               const int64_t* __restrict__ ntoff, uint32_t* __restrict__ ntab) {
+    GRID_STRIDE(f, (uint64_t)NLP[ntv]) {
+        const uint32_t i = owner_of(NLP, ntv, (int64_t)f);
+        const uint32_t v = tv[i];
+        const uint32_t len = (uint32_t)(NLP[i + 1] - NLP[i]);
+        if (len < GJ_HASH_MIN_DEG) continue;
+        const uint32_t bits = gj_tab_bits(len), mask = (1u << bits) - 1u;
+        uint32_t* t = ntab + ntoff[v];
+        const uint32_t x = nnbr[noff[v] + ((int64_t)f - NLP[i])];
+        uint32_t h = gj_tab_start(x, bits);
+        for (uint32_t probe = 0; probe <= mask; probe++) {
+            if (atomicCAS(t + h, GJ_EMPTY, x) == GJ_EMPTY) break;
+            h = (h + 1u) & mask;
+        }
     }
 }
 
@@ -389,38 +548,124 @@ void gj_csr_release(gj_csr& c) {
 
 namespace {
 
-// The next version of one index: the committed slots minus the batch's
-// deletions, merged with its (sorted) inserts, then offsets and hash sets.
-int commit_side(gj_ctx* ctx, uint32_t n, const gj_csr& cur, uint64_t m, const DeltaSide& side, gj_csr* out,
+// Arrays of c sized for n vertices, m slots and t hash-set slots, reusing
+// those it has (a spare index) when they are large enough.
+int ensure_csr(gj_ctx* ctx, gj_csr& c, uint32_t n, uint64_t m, uint64_t t) {
+    if (!c.off) GJ_CUDA_TRY(ctx, cudaMalloc(&c.off, sizeof(int64_t) * ((size_t)n + 1)));
+    if (!c.tab_off) GJ_CUDA_TRY(ctx, cudaMalloc(&c.tab_off, sizeof(int64_t) * ((size_t)n + 1)));
+    if (c.cap_m < (m ? m : 1)) {
+        if (c.nbr) cudaFree(c.nbr);
+        if (c.key) cudaFree(c.key);
+        c.nbr = c.key = nullptr;
+        c.cap_m = 0;
+        const uint64_t cap = m + m / 16 + 1024;  // room for the growth of later updates
+        GJ_CUDA_TRY(ctx, cudaMalloc(&c.nbr, sizeof(uint32_t) * cap));
+        GJ_CUDA_TRY(ctx, cudaMalloc(&c.key, sizeof(uint32_t) * cap));
+        c.cap_m = cap;
+    }
+    if (c.cap_tab < (t ? t : 1)) {
+        if (c.tab) cudaFree(c.tab);
+        c.tab = nullptr;
+        c.cap_tab = 0;
+        const uint64_t cap = t + t / 16 + 1024;
+        GJ_CUDA_TRY(ctx, cudaMalloc(&c.tab, sizeof(uint32_t) * cap));
+        c.cap_tab = cap;
+    }
+    return GJ_OK;
+}
+
+// The next version of one index, written into out (whose arrays are reused
+// when large enough). Only the touched vertices (list owners of the batch's
+// changes in this direction) are recomputed: their lists merged with the
+// changes and their hash sets rebuilt; every other list and hash set is
+// copied with the constant shift that the touched vertices before it add up
+// to (the maintenance proportional to the change of Section 3.3.2, plus one
+// coalesced copy of the untouched arrays).
+int commit_side(gj_ctx* ctx, uint32_t n, const gj_csr& cur, uint64_t m, const DeltaSide& side, gj_csr& out,
                 uint64_t* m_out) {
     cudaStream_t st = ctx->stream;
-    const uint64_t mm = m ? m : 1;
-    const uint64_t m2 = m - side.ndel + side.nins;
+    const uint64_t nk = (uint64_t)side.nins + side.ndel;  // > 0
+    // keys (and the sort's second buffer), flag, tv, then pos, dlen, S, dtab,
+    // ST, olen, OLP, nlen, NLP, ntab, NTP; every piece starts on a 256-byte boundary
+    const size_t bytes = 16 * nk + 4 * nk + 4 * nk + 11 * 8 * (nk + 1) + 14 * 256;
     char* mem = nullptr;
-    const size_t bytes = 4 * mm + 8 * (mm + 1) + 8 * mm + 4 * 256;
     GJ_CUDA_TRY(ctx, cudaMallocAsync(&mem, bytes, st));
     Arena A{mem, 0, bytes};
-    uint32_t* flag = (uint32_t*)A.take(4 * mm);
-    int64_t* pos = (int64_t*)A.take(8 * (mm + 1));
-    uint32_t* kk = (uint32_t*)A.take(4 * mm);
-    uint32_t* kn = (uint32_t*)A.take(4 * mm);
-    uint32_t kept = 0;
+    uint64_t* keys = (uint64_t*)A.take(16 * nk);
+    uint32_t* flag = (uint32_t*)A.take(4 * nk);
+    int64_t* pos = (int64_t*)A.take(8 * (nk + 1));
+    uint32_t* tv = (uint32_t*)A.take(4 * nk);
+    int64_t* dlen = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* S = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* dtab = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* ST = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* olen = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* OLP = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* nlen = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* NLP = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* ntb = (int64_t*)A.take(8 * (nk + 1));
+    int64_t* NTP = (int64_t*)A.take(8 * (nk + 1));
+    if (!NTP) {  // the pieces above must fit the allocation
+        cudaFreeAsync(mem, st);
+        gj_set_error(ctx, GJ_E_NOMEM, "update commit: arena too small");
+        return GJ_E_NOMEM;
+    }
     int rc = GJ_OK;
-    if (m) {
-        k_keep_slots<<<grid_for(ctx, m), 256, 0, st>>>(cur.key, cur.nbr, m, side, flag);
+    int64_t h[3] = {0, 0, 0};  // distinct touched vertices, growth of the lists, of the hash sets
+    uint32_t ntv = 0;
+    auto step = [&]() -> int {
+        k_touch_keys<<<grid_for(ctx, nk), 256, 0, st>>>(side.ins_key, side.nins, side.del_key, side.ndel, keys);
         GJ_LAUNCHED(ctx);
-        rc = compact_pairs(ctx, nullptr, cur.key, cur.nbr, m, 0, flag, pos, kk, kn, &kept);
-    }
-    if (rc == GJ_OK && cudaMalloc(&out->key, 4 * (size_t)(m2 ? m2 : 1)) != cudaSuccess) rc = GJ_E_NOMEM;
-    if (rc == GJ_OK && cudaMalloc(&out->nbr, 4 * (size_t)(m2 ? m2 : 1)) != cudaSuccess) rc = GJ_E_NOMEM;
-    if (rc == GJ_OK && (uint64_t)kept + side.nins > 0) {
-        k_merge_slots<<<grid_for(ctx, kept + side.nins), 256, 0, st>>>(kk, kn, kept, side.ins_key, side.ins_nbr,
-                                                                      side.nins, out->key, out->nbr);
+        uint64_t* sorted = keys;
+        GJ_TRY(gj_radix_sort_u64(ctx, keys, keys + nk, nk, vertex_bits(n), &sorted));
+        k_run_flag<<<grid_for(ctx, nk), 256, 0, st>>>(sorted, nk, flag);
         GJ_LAUNCHED(ctx);
-    }
+        GJ_TRY(gj_scan_u32(ctx, flag, pos, nk));
+        k_run_compact<<<grid_for(ctx, nk), 256, 0, st>>>(sorted, nk, flag, pos, tv);
+        GJ_LAUNCHED(ctx);
+        GJ_TRY(read_i64(ctx, pos + nk, &h[0]));
+        ntv = (uint32_t)h[0];
+        k_touch_info<<<grid_for(ctx, ntv), 256, 0, st>>>(tv, ntv, side, cur.off, dlen, dtab, olen, nlen, ntb);
+        GJ_LAUNCHED(ctx);
+        GJ_TRY(gj_scan_i64(ctx, dlen, S, ntv));
+        GJ_TRY(gj_scan_i64(ctx, dtab, ST, ntv));
+        GJ_TRY(gj_scan_i64(ctx, olen, OLP, ntv));
+        GJ_TRY(gj_scan_i64(ctx, nlen, NLP, ntv));
+        GJ_TRY(gj_scan_i64(ctx, ntb, NTP, ntv));
+        int64_t hf[3] = {0, 0, 0};  // old entries, next entries, next hash-set slots of the touched vertices
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&hf[0], OLP + ntv, 8, cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&hf[1], NLP + ntv, 8, cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&hf[2], NTP + ntv, 8, cudaMemcpyDeviceToHost, st));
+        int64_t t_old = 0;
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&h[1], S + ntv, 8, cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&h[2], ST + ntv, 8, cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&t_old, cur.tab_off + n, 8, cudaMemcpyDeviceToHost, st));
+        GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        const uint64_t m2 = (uint64_t)((int64_t)m + h[1]), t2 = (uint64_t)(t_old + h[2]);
+        GJ_TRY(ensure_csr(ctx, out, n, m2, t2));
+        k_shift_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(cur.off, cur.tab_off, n, tv, ntv, S, ST, out.off,
+                                                                         out.tab_off);
+        GJ_LAUNCHED(ctx);
+        const unsigned regions = (unsigned)(ntv + 1 < (uint64_t)ctx->sm_count * 16 ? ntv + 1 : ctx->sm_count * 16);
+        k_shift_copy<<<regions, 256, 0, st>>>(cur.off, cur.tab_off, cur.nbr, cur.key, cur.tab, n, tv, ntv, S, ST,
+                                              out.nbr, out.key, out.tab);
+        GJ_LAUNCHED(ctx);
+        k_merge_touched<<<grid_for(ctx, (uint64_t)hf[0] + side.nins), 256, 0, st>>>(cur.off, cur.nbr, tv, ntv, side,
+                                                                                     OLP, out.off, out.nbr, out.key);
+        GJ_LAUNCHED(ctx);
+        if (hf[2] > 0) {
+            k_touched_clear<<<grid_for(ctx, (uint64_t)hf[2]), 256, 0, st>>>(tv, ntv, NTP, out.tab_off, out.tab);
+            GJ_LAUNCHED(ctx);
+            k_touched_fill<<<grid_for(ctx, (uint64_t)hf[1]), 256, 0, st>>>(tv, ntv, NLP, out.off, out.nbr, out.tab_off,
+                                                                            out.tab);
+            GJ_LAUNCHED(ctx);
+        }
+        GJ_CUDA_TRY(ctx, cudaGetLastError());
+        *m_out = m2;
+        return GJ_OK;
+    };
+    rc = step();
     cudaFreeAsync(mem, st);
-    if (rc == GJ_OK) rc = gj_csr_finish(ctx, n, m2, out);
-    *m_out = m2;
     return rc;
 }
 
@@ -432,22 +677,29 @@ int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_f
         g->version++;
         return GJ_OK;
     }
-    gj_csr nf, nr;
+    // the next version goes into the previous version's arrays when there are some
+    gj_csr nf = g->spare_fwd, nr = g->spare_rev;
+    g->spare_fwd = gj_csr{};
+    g->spare_rev = gj_csr{};
     uint64_t mf = 0, mr = 0;
-    int rc = commit_side(ctx, g->n, g->fwd, g->m, d.view.fwd, &nf, &mf);
-    if (rc == GJ_OK) rc = commit_side(ctx, g->n, g->rev, g->m, d.view.rev, &nr, &mr);
-    if (rc != GJ_OK) {
+    int rc = commit_side(ctx, g->n, g->fwd, g->m, d.view.fwd, nf, &mf);
+    if (rc == GJ_OK) rc = commit_side(ctx, g->n, g->rev, g->m, d.view.rev, nr, &mr);
+    if (rc == GJ_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        gj_set_error(ctx, GJ_E_CUDA, "update commit: the index kernels failed");
+        rc = GJ_E_CUDA;
+    }
+    if (rc != GJ_OK) {  // the committed graph is unchanged
         gj_csr_release(nf);
         gj_csr_release(nr);
         return rc;
     }
-    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    if (old_fwd && old_rev) {
+    if (old_fwd && old_rev) {  // readers still in flight keep the previous arrays
         *old_fwd = g->fwd;
         *old_rev = g->rev;
     } else {
-        gj_csr_release(g->fwd);
-        gj_csr_release(g->rev);
+        g->spare_fwd = g->fwd;
+        g->spare_rev = g->rev;
     }
     g->fwd = nf;
     g->rev = nr;

@@ -52,6 +52,9 @@ struct gj_csr {
     uint32_t* key = nullptr;     // [m]
     int64_t* tab_off = nullptr;  // [n + 1]
     uint32_t* tab = nullptr;     // [tab_off[n]]
+    // allocated lengths of nbr/key and tab (0: exactly m and tab_off[n]); an
+    // index kept as the spare of an update can take a larger one in place
+    uint64_t cap_m = 0, cap_tab = 0;
 };
 
 constexpr uint32_t GJ_HASH_MIN_DEG = 16;
@@ -103,6 +106,7 @@ struct gj_graph {
     gj_csr fwd;  // out-neighbours
     gj_csr rev;  // in-neighbours
     gj_tri tri;  // triangle index (built on request; dropped when the graph changes)
+    gj_csr spare_fwd, spare_rev;  // the previous version's arrays, reused by the next update's commit
     uint32_t* relabel = nullptr;  // new id of each input id (degree renaming), null = identity
     uint32_t load_flags = 0;
     GraphView view() const {
@@ -252,6 +256,16 @@ struct gj_ctx {
 // misses one warp (it ends by its time bound), or its counts start just
 // below 2^63 (they overflow).
 enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2 };
+
+// Engine of a batch's delta queries: the level-synchronous one spreads a
+// small batch's fan-out over the whole GPU at once, the fused one balances
+// a large batch's work better; GJ_FLAG_DELTA_PLAIN / _FUSED force either.
+constexpr uint64_t GJ_DELTA_FUSED_MIN = 32768;  // normalised changes from which the fused engine runs
+inline uint32_t gj_delta_engine(const gj_ctx* ctx, uint64_t changes) {
+    if (ctx->opt.flags & GJ_FLAG_DELTA_PLAIN) return GJ_ENGINE_PLAIN;
+    if (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) return GJ_ENGINE_FUSED;
+    return changes >= GJ_DELTA_FUSED_MIN ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN;
+}
 
 inline uint64_t gj_wait_ns(const gj_ctx* ctx) { return (uint64_t)(ctx->wait_ms ? ctx->wait_ms : 10000) * 1000000ull; }
 

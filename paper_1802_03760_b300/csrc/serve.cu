@@ -244,7 +244,7 @@ bool run_batch(gj_server* S) {
     DeltaBuf buf;
     int rc = gj_delta_prepare(ctx, g, r->src.data(), r->dst.data(), r->sign.data(), r->src.size(), &buf);
     if (rc == GJ_OK) rc = gj_delta_eval(ctx, g, buf.batch, r->qs.data(), nq,
-                                         (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) ? GJ_ENGINE_FUSED : GJ_ENGINE_PLAIN,
+                                         gj_delta_engine(ctx, buf.batch.n),
                                          c.data(), h.data());
     Retired rt;
     const uint64_t changes = buf.batch.n;

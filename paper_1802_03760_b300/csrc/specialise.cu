@@ -333,7 +333,7 @@ int gj_graph_transform(gj_ctx* ctx, gj_graph* g, uint32_t flags) {
         gj_set_error(ctx, GJ_E_CUDA, std::string("degree renaming: ") + cudaGetErrorString(e));
         return GJ_E_CUDA;
     }
-    for (gj_csr* c : {&g->fwd, &g->rev}) gj_csr_release(*c);
+    for (gj_csr* c : {&g->fwd, &g->rev, &g->spare_fwd, &g->spare_rev}) gj_csr_release(*c);
     gj_tri_release(g->tri);
     int rc = gj_csr_build(ctx, pairs, pairs + m, m, n, g);
     cudaFreeAsync(pairs, st);

@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gj.h")
 ENGINE_PLAIN = 0
 ENGINE_FUSED = 1
 FLAG_DELTA_FUSED = 1
+FLAG_DELTA_PLAIN = 2
 LOAD_SYMMETRIZE = 1
 LOAD_DEGREE_ORDER = 2
 LOAD_ORIENT = 4

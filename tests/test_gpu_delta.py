@@ -15,10 +15,11 @@ M64 = (1 << 64) - 1
 NAMES = sorted(QUERIES)
 
 
-@pytest.fixture(scope="module", params=[0, gj.FLAG_DELTA_FUSED], ids=["level-sync", "fused"])
+@pytest.fixture(scope="module", params=[gj.FLAG_DELTA_PLAIN, gj.FLAG_DELTA_FUSED, 0],
+                ids=["level-sync", "fused", "by-size"])
 def ctx(request):
-    """Delta queries run on the level-synchronous engine unless the context asks
-    for the fused one: both are checked."""
+    """Delta queries on the level-synchronous engine, on the fused one, and
+    chosen by batch size (the default): all are checked."""
     c = gj.Context(0, flags=request.param)
     yield c
     c.close()
@@ -161,3 +162,40 @@ def test_device_batch_inputs(ctx):
                             torch.from_numpy(bg).cuda(), [q])
     oq = oracle.Query(*QUERIES["triangle"])
     assert dc[0] == og2.count(oq)[0] - og.count(oq)[0]
+
+
+def test_commits_reuse_arrays_and_move_hash_sets(ctx):
+    """A long stream of batches on one graph: each commit writes the next
+    version into the previous version's arrays (shifting untouched lists and
+    hash sets, rebuilding the touched ones). Lists cross the hash-set
+    threshold of 16 entries both ways, and the exported index and every count
+    equal the oracle's after each batch."""
+    rng = np.random.default_rng(77)
+    n = 300
+    # vertex 5 has 15 out-neighbours (no hash set); vertex 9 has 17 (a hash set)
+    s = np.concatenate([np.full(15, 5), np.full(17, 9), rng.integers(0, n, 2500)]).astype(np.uint32)
+    d = np.concatenate([np.arange(20, 35), np.arange(40, 57), rng.integers(0, n, 2500)]).astype(np.uint32)
+    og = oracle.Graph(n, s, d)
+    g = gj.Graph(ctx, s, d, n)
+    names = ["triangle", "diamond", "4-clique"]
+    qs = [gj.Query(ctx, *QUERIES[nm]) for nm in names]
+    oqs = [oracle.Query(*QUERIES[nm]) for nm in names]
+    fixed = [
+        (np.array([5, 5, 9, 9, 9], np.uint32), np.array([100, 101, 40, 41, 42], np.uint32),
+         np.array([1, 1, -1, -1, -1], np.int8)),  # 5 -> 17 entries, 9 -> 14
+        (np.array([5, 5, 5, 9, 9], np.uint32), np.array([100, 20, 21, 40, 200], np.uint32),
+         np.array([-1, -1, -1, 1, 1], np.int8)),  # 5 -> 14, 9 -> 16
+    ]
+    for step in range(12):
+        bs, bd, bg = fixed[step] if step < 2 else random_batch(rng, n, og.edges(), int(rng.integers(1, 400)))
+        (cs, cd, cg), og2 = oracle.apply_batch(og, bs, bd, bg)
+        dc, dh = gj.apply_batch(g, bs, bd, bg, qs)
+        for i, q in enumerate(oqs):
+            c0, h0 = og.count(q)
+            c1, h1 = og2.count(q)
+            assert (dc[i], dh[i]) == (c1 - c0, (h1 - h0) & M64), (step, names[i])
+            assert gj.count(g, qs[i]) == (c1, h1), (step, names[i])
+        off, nbr = g.export()
+        es, ed = og2.edges()
+        assert np.array_equal(nbr, ed) and np.array_equal(np.repeat(np.arange(n), np.diff(off)), es), step
+        og = og2
