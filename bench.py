@@ -728,8 +728,8 @@ def run_multi(args):
     g = gj.Graph(ctx, ds, dd, n)
     build_s = time.perf_counter() - t0
     hi = max(1, min(n, args.sample_vertices))
-    # launch settings from a smaller sample (the level-synchronous budget on every 8th query)
-    tune = gj.autotune(g, qs[::8], v_range=(0, max(1, hi // 4)), prefix_cap_bytes=2 << 30)
+    # launch settings chosen on the sample itself (untimed)
+    tune = gj.autotune(g, qs, v_range=(0, hi), prefix_cap_bytes=2 << 30)
     times = []
     res = None
     for i in range(args.warmup + args.steps):

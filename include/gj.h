@@ -295,7 +295,8 @@ int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
  * Chooses the context's launch settings by timing the given queries on the
  * first-attribute range [v_lo, v_hi) of g (a sample of the workload): seeds
  * per grab in {32, 64, 128, 256} x {all, all but one} resident blocks per SM
- * for the fused engine, and a prefix-buffer budget in {64 MiB, 256 MiB,
+ * x donation when warps idle or whenever a queue slot is free for the fused
+ * engine, and a prefix-buffer budget in {64 MiB, 256 MiB,
  * 1 GiB, 2 GiB} up to prefix_cap_bytes (0 = 2 GiB) for the level-synchronous
  * engine (the memory/runtime trade-off of the paper's batch size). Applies
  * the fastest settings to g's context and returns them. Errors:

@@ -460,12 +460,13 @@ int gj_autotune(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t pr
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     // on any failure the context keeps the settings it had before the call
-    const uint32_t old_chunk = ctx->seed_chunk, old_bps = ctx->blocks_per_sm;
+    const uint32_t old_chunk = ctx->seed_chunk, old_bps = ctx->blocks_per_sm, old_don = ctx->donation;
     const uint64_t old_bytes = ctx->opt.prefix_buffer_bytes;
     const int rc = autotune_sweep(g, qs, nq, prefix_cap_bytes, v_lo, v_hi, out);
     if (rc != GJ_OK) {
         ctx->seed_chunk = old_chunk;
         ctx->blocks_per_sm = old_bps;
+        ctx->donation = old_don;
         ctx->opt.prefix_buffer_bytes = old_bytes;
     }
     return rc;
@@ -499,23 +500,28 @@ int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t
         per_sm_max = gj_fused_occupancy(ctx, kmax, ext);
     }
     double best_f = 1e300;
-    uint32_t best_chunk = 32, best_bps = 0;
+    uint32_t best_chunk = 32, best_bps = 0, best_don = 0;
     for (uint32_t chunk : {32u, 64u, 128u, 256u}) {
         for (int bps : {0, per_sm_max - 1}) {  // 0: as many blocks as fit
             if (bps < 0) continue;
-            ctx->seed_chunk = chunk;
-            ctx->blocks_per_sm = (uint32_t)bps;
-            double ms = 0;
-            GJ_TRY(timed(GJ_ENGINE_FUSED, &ms));
-            if (ms < best_f) {
-                best_f = ms;
-                best_chunk = chunk;
-                best_bps = (uint32_t)bps;
+            for (uint32_t don : {0u, 1u}) {  // donate when warps idle / whenever a slot is free
+                ctx->seed_chunk = chunk;
+                ctx->blocks_per_sm = (uint32_t)bps;
+                ctx->donation = don;
+                double ms = 0;
+                GJ_TRY(timed(GJ_ENGINE_FUSED, &ms));
+                if (ms < best_f) {
+                    best_f = ms;
+                    best_chunk = chunk;
+                    best_bps = (uint32_t)bps;
+                    best_don = don;
+                }
             }
         }
     }
     ctx->seed_chunk = best_chunk;
     ctx->blocks_per_sm = best_bps;
+    ctx->donation = best_don;
     // plain engine: prefix-buffer budget, at most prefix_cap_bytes
     if (!prefix_cap_bytes) prefix_cap_bytes = 2ull << 30;
     double best_p = 1e300;
