@@ -394,7 +394,28 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         }
     };
 
+    // The count step runs from one place (one inlined copy of its code): the
+    // branches that descend to a level set act (and, for a donated candidate
+    // range, its bounds) and loop back here.
+    int act = -1;
+    bool act_stats = true, act_ranged = false;
+    unsigned long long act_lo = 0, act_hi = 0;
     while (true) {
+        if (act >= 0) {
+            activate(act, act_stats);
+            if (act_ranged) {
+                if (lane == 0) {
+                    cur_[act] = act_lo;
+                    if (act_hi < tot_[act]) tot_[act] = act_hi;
+                }
+                __syncwarp();
+            }
+            depth = act;
+            act = -1;
+            act_stats = true;
+            act_ranged = false;
+            continue;
+        }
         if (depth == 1) {
             // ---------------- take seeds, 32 at a time from the grabbed range
             if (gpos >= gend) {
@@ -406,8 +427,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const uint64_t g = gpos;
             if (g >= space) {
                 if (k > 2 && n_[2] > 0) {
-                    activate(2);
-                    depth = 2;
+                    act = 2;
                     continue;
                 }
                 if (!A.Q.b) break;
@@ -494,16 +514,12 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     atomicExch(A.Q.seq + (took & mask), (unsigned long long)took + A.Q.cap);  // free the slot
                 }
                 __syncwarp();
-                const bool ranged = c_hi != ~0ull;
-                activate((int)L, !ranged);  // a candidate range of a batch already counted by its giver
-                if (ranged) {
-                    if (lane == 0) {
-                        cur_[L] = c_lo;
-                        if (c_hi < tot_[L]) tot_[L] = c_hi;
-                    }
-                    __syncwarp();
-                }
-                depth = (int)L;
+                // a candidate range of a batch already counted by its giver is not counted again
+                act = (int)L;
+                act_ranged = c_hi != ~0ull;
+                act_stats = !act_ranged;
+                act_lo = c_lo;
+                act_hi = c_hi;
                 continue;
             }
             // query owning this chunk: last q with qbase[q] <= g
@@ -515,8 +531,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const int q = (int)lo;
             if (q != cur_q) {
                 if (k > 2 && n_[2] > 0) {  // finish the other query's prefixes first (g is read later)
-                    activate(2);
-                    depth = 2;
+                    act = 2;
                     continue;
                 }
                 flush_q();
@@ -581,10 +596,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 stat_add(A.stats, 3, 2, __popc(mask));
             }
             __syncwarp();
-            if (n_[2] >= FT) {
-                activate(2);
-                depth = 2;
-            }
+            if (n_[2] >= FT) act = 2;
             continue;
         }
 
@@ -927,16 +939,12 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 if (!last) n_[j + 1] = nn;
             }
             __syncwarp();
-            if (descend) {
-                activate(j + 1);
-                depth = j + 1;
-            }
+            if (descend) act = j + 1;
             continue;
         }
         // level j has no proposals left
         if (j + 1 < (int)k && n_[j + 1] > 0) {
-            activate(j + 1);
-            depth = j + 1;
+            act = j + 1;
             continue;
         }
         if (lane == 0) n_[j] = 0;
