@@ -271,13 +271,13 @@ typedef struct {
      * 2: off. Results never depend on it. */
     uint32_t donation;
     /* The fused engine's end-of-launch wait (warps without work waiting for
-     * donations until every warp is idle) gives up with GJ_E_TIMEOUT once the
+     * donations until no warp holds work) gives up with GJ_E_TIMEOUT once the
      * donation queue has shown no progress for wait_ms milliseconds; 0 =
      * 10000. Working warps interact with the queue at least every ~1000
      * candidates, so the bound only ends waits that cannot end otherwise. */
     uint32_t wait_ms;
     /* Failure injection for tests; 0 = off. 1: the end-of-launch wait counts
-     * one more warp than the launch has, so it can only end by its time bound
+     * a working warp that never finishes, so it can only end by its time bound
      * (the count call returns GJ_E_TIMEOUT; the context stays usable). 2: the
      * fused engine's per-query counts start at 2^63 - 1024, so a query with
      * more than 1023 matches returns GJ_E_OVERFLOW. */
@@ -355,11 +355,15 @@ int gj_graph_last_batch(const gj_graph* g, uint64_t* changes);
  * admitted against a device-memory budget. While serving, use only
  * gj_submit_count, gj_submit_batch, gj_poll and gj_serve_stop on the
  * context; other calls on it return GJ_E_INVALID. Queries passed to a
- * request must stay alive until the request is polled.
+ * request must stay alive until the request is polled. Each count launch
+ * (a wave) balances its warps through a work-donation queue of its own, set
+ * by the context's donation and wait_ms settings at the time of the launch.
  */
 typedef struct {
     uint64_t req_id;
-    int32_t status;          /* GJ_OK, or the request's own error (e.g. GJ_E_ADMIT) */
+    int32_t status;          /* GJ_OK, or the request's own error: GJ_E_ADMIT, GJ_E_OVERFLOW (a
+                              * count of its wave passed 2^63 - 1), GJ_E_TIMEOUT (its wave's
+                              * bounded donation wait expired), GJ_E_CUDA */
     uint32_t kind;           /* 0 = count request, 1 = update batch */
     uint32_t nq;
     uint32_t reserved;

@@ -43,9 +43,14 @@ constexpr uint64_t RANGE_SPLIT_MIN = 4096;  // remaining candidates worth splitt
 // every slot carries a sequence number (free for ticket t when seq == t,
 // holding ticket t's bundle when seq == t + 1). A giver reserves ticket
 // tail only if its slot is free and never waits; a taker takes ticket head
-// only once it is published and frees the slot for ticket head + cap. idle
-// counts warps without work; the launch ends when every warp is idle and
-// head == tail (only working warps give, so nothing can arrive after that).
+// only once it is published and frees the slot for ticket head + cap.
+// busy counts the warps that hold work: a warp counts itself from its start
+// until it runs out of seeds, and again from just before it claims a bundle
+// until it has finished it. A warp without work leaves once busy == 0 and
+// head == tail: only busy warps give, so nothing can arrive after that. The
+// rule waits only on warps that have started, so the launch needs no
+// co-resident grid and can share the GPU with other launches. idle counts
+// the waiting warps (a hint for givers).
 struct DonationQueue {
     Bundle* b = nullptr;  // null: donation off
     uint32_t cap = 0;     // power of two
@@ -53,8 +58,8 @@ struct DonationQueue {
     unsigned long long* tail = nullptr;
     unsigned long long* seq = nullptr;  // [cap]
     unsigned int* idle = nullptr;
-    unsigned int* err = nullptr;  // set when the bounded idle wait gives up
-    unsigned int nwarps = 0;
+    unsigned int* busy = nullptr;
+    unsigned long long* err = nullptr;  // set when the bounded wait gives up
     unsigned int always = 0;  // 1: give whenever a slot is free (stress setting)
 };
 
@@ -237,6 +242,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     const uint64_t space = A.qbase[A.nq];
 
     if (lane < GJ_MAX_K) { n_[lane] = 0; cur_[lane] = 0; tot_[lane] = 0; ip_[lane] = 0; }
+    if (lane == 0 && A.Q.b) atomicAdd(A.Q.busy, 1u);  // before the first grab of seeds
     __syncwarp();
     const DeltaView* Dv = DELTA ? &A.D : nullptr;
 
@@ -431,17 +437,18 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     continue;
                 }
                 if (!A.Q.b) break;
-                // No seeds left: take a donated bundle, or wait until every
-                // warp is idle and none is left. The wait is bounded: it gives
-                // up once the queue (head, tail, idle count) has not changed
-                // for A.wait_ns, or once another warp has given up.
+                // No seeds left: take a donated bundle, or wait until no warp
+                // holds work and none is left. The wait is bounded: it gives
+                // up once the queue (head, tail, idle and busy counts) has not
+                // changed for A.wait_ns, or once another warp has given up.
                 const unsigned long long mask = A.Q.cap - 1;
                 long long took = -1;
                 bool idle_marked = false, give_up = false;
                 uint32_t backoff = 64;  // ns; doubles while nothing is published (less polling traffic)
                 unsigned long long seen_h = ~0ull, seen_t = ~0ull;
-                unsigned int seen_i = ~0u;
+                unsigned int seen_i = ~0u, seen_b = ~0u;
                 uint64_t since = globaltimer_ns();
+                if (lane == 0) atomicSub(A.Q.busy, 1u);
                 while (true) {
                     long long b = -1;
                     if (lane == 0) {
@@ -449,22 +456,30 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         if (vload64(A.Q.seq + (h & mask)) == h + 1) {  // published
                             if (idle_marked) atomicSub(A.Q.idle, 1u);
                             idle_marked = false;
+                            atomicAdd(A.Q.busy, 1u);  // before the claim, so that busy == 0 never hides it
                             if (atomicCAS(A.Q.head, h, h + 1) == h) b = (long long)h;
+                            else atomicSub(A.Q.busy, 1u);
                         } else if (h == vload64(A.Q.tail)) {  // empty
                             if (!idle_marked) atomicAdd(A.Q.idle, 1u);
                             idle_marked = true;
-                            if (vload(A.Q.idle) == A.Q.nwarps && vload64(A.Q.head) == vload64(A.Q.tail)) b = -2;
+                            if (vload(A.Q.busy) == 0u) {
+                                // a giver fences between its reservation and its
+                                // leaving busy: read busy first, then the queue
+                                __threadfence();
+                                if (vload64(A.Q.head) == vload64(A.Q.tail)) b = -2;
+                            }
                         }
                         if (b == -1) {
                             const unsigned long long t = vload64(A.Q.tail);
-                            const unsigned int iw = vload(A.Q.idle);
+                            const unsigned int iw = vload(A.Q.idle), bw = vload(A.Q.busy);
                             const uint64_t now = globaltimer_ns();
-                            if (h != seen_h || t != seen_t || iw != seen_i) {
+                            if (h != seen_h || t != seen_t || iw != seen_i || bw != seen_b) {
                                 seen_h = h;
                                 seen_t = t;
                                 seen_i = iw;
+                                seen_b = bw;
                                 since = now;
-                            } else if (now - since > A.wait_ns || vload(A.Q.err)) {
+                            } else if (now - since > A.wait_ns || vload64(A.Q.err)) {
                                 b = -3;
                             }
                         }
@@ -484,7 +499,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     if (backoff < 16384) backoff <<= 1;
                 }
                 if (give_up) {
-                    if (lane == 0) atomicExch(A.Q.err, 1u);
+                    if (lane == 0) atomicExch(A.Q.err, 1ull);
                     break;
                 }
                 if (took < 0) break;
@@ -1011,19 +1026,14 @@ int fused_cfg(gj_ctx* ctx, uint32_t kmax, const Plan* plans, uint32_t n, FusedCf
     return ext ? fused_cfg_t<DELTA, true>(ctx, kmax, true, c) : fused_cfg_t<DELTA, false>(ctx, kmax, true, c);
 }
 
-// With donation on, warps wait for one another at the end of the launch,
-// so every block must be resident at once: a cooperative launch guarantees
-// that (the grid is sized from the occupancy of an idle GPU).
+// An ordinary launch: the end-of-launch wait of the donation queue waits
+// only on warps that have started, so blocks need not be co-resident (the
+// grid is one persistent wave on an idle GPU; on a shared one, as in
+// serving, later blocks start as earlier launches leave room).
 template <bool DELTA, bool EXT>
 int launch_t(gj_ctx* ctx, FusedArgs& A, unsigned grid, int smem, cudaStream_t st) {
-    if (A.Q.b) {
-        void* args[] = {&A};
-        GJ_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)k_fused<DELTA, EXT>, dim3(grid), dim3(FW * 32), args,
-                                                     (size_t)smem, st));
-    } else {
-        k_fused<DELTA, EXT><<<grid, FW * 32, smem, st>>>(A);
-        GJ_CUDA_TRY(ctx, cudaGetLastError());
-    }
+    k_fused<DELTA, EXT><<<grid, FW * 32, smem, st>>>(A);
+    GJ_CUDA_TRY(ctx, cudaGetLastError());
     GJ_LAUNCHED(ctx);
     return GJ_OK;
 }
@@ -1036,40 +1046,58 @@ int launch_fused(gj_ctx* ctx, FusedArgs& A, const FusedCfg& c, cudaStream_t st) 
 
 }  // namespace
 
-constexpr uint32_t DONATION_CAP = 16384;  // ring slots (power of two)
+constexpr uint32_t DONATION_CAP = 16384;  // ring slots of a context's queue (power of two)
+constexpr uint32_t WAVE_DONATION_CAP = 2048;  // ring slots of a served wave's own queue
 
-// Donation queue in scratch slot 4: ring of DONATION_CAP bundles, counters
-// cleared and slot sequence numbers reset.
-static int donation_queue(gj_ctx* ctx, unsigned int nwarps, DonationQueue* Q) {
-    const size_t bundles = sizeof(Bundle) * (size_t)DONATION_CAP;
-    const size_t seqb = sizeof(unsigned long long) * (size_t)DONATION_CAP;
-    const size_t ctrb = 4 * 256;  // head, tail, idle, err each on its own 256-byte line
-    char* base = nullptr;
-    GJ_TRY(gj_scratch(ctx, 4, bundles + seqb + ctrb + 512, (void**)&base));
-    char* p = base + ((bundles + 255) & ~(size_t)255);
+// Bytes of a donation queue of cap slots: the bundles, their sequence
+// numbers and the counters head, tail, idle and busy, each on its own
+// 256-byte line.
+static size_t queue_bytes(uint32_t cap) {
+    return ((sizeof(Bundle) * (size_t)cap + 255) & ~(size_t)255) +
+           ((sizeof(unsigned long long) * (size_t)cap + 255) & ~(size_t)255) + 4 * 256;
+}
+
+// Lays a queue of cap slots out at base (256-byte aligned) and enqueues on
+// st the reset of its counters and slot sequence numbers; err is the
+// launch's give-up flag (a zeroed device word).
+static int queue_init(gj_ctx* ctx, char* base, uint32_t cap, unsigned long long* err, cudaStream_t st,
+                      DonationQueue* Q) {
+    char* p = base + ((sizeof(Bundle) * (size_t)cap + 255) & ~(size_t)255);
     unsigned long long* seq = (unsigned long long*)p;
-    unsigned long long* ctr = (unsigned long long*)(p + ((seqb + 255) & ~(size_t)255));
-    GJ_CUDA_TRY(ctx, cudaMemsetAsync(ctr, 0, ctrb, ctx->stream));
-    k_queue_init<<<64, 256, 0, ctx->stream>>>(seq, DONATION_CAP);
+    unsigned long long* ctr = (unsigned long long*)(p + ((sizeof(unsigned long long) * (size_t)cap + 255) & ~(size_t)255));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(ctr, 0, 4 * 256, st));
+    // failure injection for tests: the queue starts with one busy warp that
+    // never leaves, so the end-of-launch wait can only end by its time bound
+    // (GJ_E_TIMEOUT)
+    if (ctx->fault == GJ_FAULT_WAIT) GJ_CUDA_TRY(ctx, cudaMemsetAsync(ctr + 96, 1, 1, st));
+    k_queue_init<<<64, 256, 0, st>>>(seq, cap);
     GJ_LAUNCHED(ctx);
     Q->b = (Bundle*)base;
-    Q->cap = DONATION_CAP;
+    Q->cap = cap;
     Q->head = ctr;
     Q->tail = ctr + 32;
     Q->idle = (unsigned int*)(ctr + 64);
-    Q->err = (unsigned int*)(ctr + 96);
+    Q->busy = (unsigned int*)(ctr + 96);
+    Q->err = err;
     Q->seq = seq;
-    // failure injection for tests: the end-of-launch wait counts a warp that
-    // never arrives, so it can only end by its time bound (GJ_E_TIMEOUT)
-    Q->nwarps = nwarps + (ctx->fault == GJ_FAULT_WAIT ? 1u : 0u);
     Q->always = ctx->donation == 1 ? 1u : 0u;
     if (ctx->donation == 2) Q->b = nullptr;  // off
     return GJ_OK;
 }
 
+// Donation queue of a synchronous launch, in scratch slot 4; its give-up
+// flag sits on a line of its own after the counters.
+static int donation_queue(gj_ctx* ctx, DonationQueue* Q) {
+    char* base = nullptr;
+    GJ_TRY(gj_scratch(ctx, 4, queue_bytes(DONATION_CAP) + 256, (void**)&base));
+    unsigned long long* err = (unsigned long long*)(base + queue_bytes(DONATION_CAP));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, sizeof(*err), ctx->stream));
+    return queue_init(ctx, base, DONATION_CAP, err, ctx->stream, Q);
+}
+
 static int donation_check(gj_ctx* ctx, const DonationQueue& Q) {
     if (!Q.b) return GJ_OK;
-    unsigned int err = 0;
+    unsigned long long err = 0;
     GJ_CUDA_TRY(ctx, cudaMemcpy(&err, Q.err, sizeof(err), cudaMemcpyDeviceToHost));
     if (err) {
         gj_set_error(ctx, GJ_E_TIMEOUT, "fused engine: a bounded wait of the work-donation queue expired");
@@ -1093,10 +1121,15 @@ size_t gj_fused_async_bytes(uint32_t nq) {
     return plan_bytes + 8 * (4 * (size_t)nq + 2) + 8 * (2 * (size_t)nq) + 8 * 64 + 1024;
 }
 
+size_t gj_fused_wave_bytes(uint32_t nq) {
+    return ((gj_fused_async_bytes(nq) + 255) & ~(size_t)255) + queue_bytes(WAVE_DONATION_CAP);
+}
+
 // Enqueues one fused launch over nq plans on stream st, with all device
-// state in dscratch (gj_fused_async_bytes(nq) bytes); nothing waits. On
-// completion the counts and checksums are at *results: nq counts followed
-// by nq checksums.
+// state, its own donation queue included, in dscratch
+// (gj_fused_wave_bytes(nq) bytes); nothing waits. On completion *results
+// holds nq counts, nq checksums and two flags: the donation queue's bounded
+// wait gave up (GJ_E_TIMEOUT), a count passed 2^63 - 1 (GJ_E_OVERFLOW).
 int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t nq, cudaStream_t st, void* dscratch,
                      unsigned long long** results) {
     const size_t plan_bytes = ((sizeof(Plan) * nq) + 255) & ~(size_t)255;
@@ -1107,19 +1140,22 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
     uint64_t* qbase = (uint64_t*)(seed_n + nq);
     unsigned long long* counts_d = (unsigned long long*)(qbase + nq + 1);
     unsigned long long* chks_d = counts_d + nq;
-    unsigned long long* next = chks_d + nq;
+    unsigned long long* flags = chks_d + nq;  // [2] give-up, overflow
+    unsigned long long* next = flags + 2;
     unsigned long long* stats = next + 1;
     uint32_t kmax = 2;
     for (uint32_t q = 0; q < nq; q++) kmax = hp[q].k > kmax ? hp[q].k : kmax;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, hp, sizeof(Plan) * nq, cudaMemcpyHostToDevice, st));
-    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 1 + NSTAT), st));
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nq + 3 + NSTAT), st));
     k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nq, G, 0, G.n, seed_lo, seed_n, qbase, 0, ctx->seed_chunk);
     GJ_LAUNCHED(ctx);
     FusedCfg cfg;
     GJ_TRY(fused_cfg<false>(ctx, kmax, hp, nq, &cfg));
-    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, stats + 45};
+    FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, flags + 1};
     A.chunk = ctx->seed_chunk;
     A.wait_ns = gj_wait_ns(ctx);
+    char* qmem = base + ((gj_fused_async_bytes(nq) + 255) & ~(size_t)255);
+    GJ_TRY(queue_init(ctx, qmem, WAVE_DONATION_CAP, flags, st, &A.Q));
     GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     *results = counts_d;
     return GJ_OK;
@@ -1163,8 +1199,7 @@ int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, u
     FusedArgs A{G, d_plans, nq, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, stats + 45};
     A.chunk = ctx->seed_chunk;
     A.wait_ns = gj_wait_ns(ctx);
-    const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
-    GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
+    GJ_TRY(donation_queue(ctx, &A.Q));
     gj_timer_begin(ctx);
     GJ_TRY(launch_fused<false>(ctx, A, cfg, st));
     gj_timer_end(ctx);
@@ -1380,8 +1415,7 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         A.wait_ns = gj_wait_ns(ctx);
         A.D = batch.view;
         A.B = batch;
-        const unsigned grid = (unsigned)(ctx->sm_count * cfg.per_sm);
-        GJ_TRY(donation_queue(ctx, grid * FW, &A.Q));
+        GJ_TRY(donation_queue(ctx, &A.Q));
         gj_timer_begin(ctx);
         GJ_TRY(launch_fused<true>(ctx, A, cfg, st));
         gj_timer_end(ctx);

@@ -343,6 +343,9 @@ int gj_delta_eval(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums);
 size_t gj_fused_async_bytes(uint32_t nq);
+// Device bytes of one served wave of nq plans (gj_fused_enqueue): the
+// launch's arguments and its own donation queue.
+size_t gj_fused_wave_bytes(uint32_t nq);
 // Resident blocks per SM of the static fused kernel for queries of up to kmax
 // attributes (ext: the variant for tri atoms, inequalities or aggregation).
 int gj_fused_occupancy(gj_ctx* ctx, uint32_t kmax, bool ext);

@@ -101,8 +101,14 @@ void reap(gj_server* S) {
             i++;
             continue;
         }
-        const int st = (q == cudaSuccess) ? GJ_OK : GJ_E_CUDA;
+        int st = (q == cudaSuccess) ? GJ_OK : GJ_E_CUDA;
         if (q != cudaSuccess) cudaGetLastError();
+        // the wave's flags: its donation queue's bounded wait gave up, a
+        // count passed 2^63 - 1 (not known which: every request of the wave
+        // is refused)
+        const bool gave_up = st == GJ_OK && w->hres[2 * (size_t)w->nq] != 0;
+        const bool wave_ovf = st == GJ_OK && w->hres[2 * (size_t)w->nq + 1] != 0;
+        if (gave_up) st = GJ_E_TIMEOUT;
         uint32_t o = 0;
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -118,7 +124,7 @@ void reap(gj_server* S) {
                 }
                 o += nq;
                 r->version = w->version;
-                finish(S, r, (st == GJ_OK && ovf) ? GJ_E_OVERFLOW : st);
+                finish(S, r, (st == GJ_OK && (ovf || wave_ovf)) ? GJ_E_OVERFLOW : st);
             }
             S->in_use -= w->mem;
         }
@@ -166,7 +172,7 @@ bool launch_wave(gj_server* S) {
         while (!S->pending.empty() && S->pending.front()->kind == REQ_COUNT) {
             Request* r = S->pending.front();
             if (nq + r->qs.size() > WAVE_MAX_QUERIES && nq > 0) break;
-            const size_t need = gj_fused_async_bytes(nq + (uint32_t)r->qs.size());
+            const size_t need = gj_fused_wave_bytes(nq + (uint32_t)r->qs.size());
             if (S->in_use + need > S->budget && !take.empty()) break;
             if (S->in_use + need > S->budget && !S->inflight.empty()) break;
             S->pending.pop_front();
@@ -182,7 +188,7 @@ bool launch_wave(gj_server* S) {
     Wave* w = new Wave();
     w->reqs = take;
     w->nq = (uint32_t)plans.size();
-    w->mem = gj_fused_async_bytes(w->nq);
+    w->mem = gj_fused_wave_bytes(w->nq);
     w->version = S->g->version;
     gj_ctx* ctx = S->ctx;
     int rc = GJ_OK;
@@ -194,7 +200,7 @@ bool launch_wave(gj_server* S) {
     }
     if (rc == GJ_OK) rc = gj_fused_enqueue(ctx, S->g->view(), plans.data(), w->nq, S->s_count, w->dscratch, &w->dres);
     if (rc == GJ_OK &&
-        cudaMemcpyAsync(w->hres, w->dres, 16 * (size_t)w->nq, cudaMemcpyDeviceToHost, S->s_count) != cudaSuccess)
+        cudaMemcpyAsync(w->hres, w->dres, 16 * (size_t)w->nq + 16, cudaMemcpyDeviceToHost, S->s_count) != cudaSuccess)
         rc = GJ_E_CUDA;
     if (rc == GJ_OK && cudaEventRecord(w->done, S->s_count) != cudaSuccess) rc = GJ_E_CUDA;
     if (rc != GJ_OK) {

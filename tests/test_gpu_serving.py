@@ -3,7 +3,10 @@ overlap on the device (count waves merged into one fused launch, update
 batches running while earlier waves still read the previous index) must
 give exactly the results of running the same requests one by one, in
 submission order, through the synchronous API; and a request must give the
-same result alone as in the mix."""
+same result alone as in the mix. Each wave balances its warps through a
+donation queue of its own; forcing every batch through it changes no
+result, and a wave whose bounded wait gives up fails its requests with
+GJ_E_TIMEOUT without stopping the loop."""
 import numpy as np
 import pytest
 
@@ -48,8 +51,10 @@ def replay(s, d, n, reqs):
     return out
 
 
-def serve(s, d, n, reqs, budget=0):
+def serve(s, d, n, reqs, budget=0, **tuning):
     ctx = gj.Context(0)
+    if tuning:
+        gj.set_tuning(ctx, **tuning)
     g = gj.Graph(ctx, s, d, n)
     qmap = {nm: gj.Query(ctx, *QUERIES[nm]) for nm in QUERIES}
     srv = gj.Server(g, budget)
@@ -74,6 +79,36 @@ def test_mixed_stream_equals_sequential_replay():
         assert (r["counts"], r["checksums"]) == (c, h), (i, reqs[i][0], reqs[i][2])
         assert r["version"] == ver, i
         assert r["end_ms"] >= r["start_ms"] >= r["submit_ms"]
+
+
+def test_waves_with_forced_donation_equal_sequential_replay():
+    scale = 12
+    s, d, reqs = make_requests(53, scale, 24)
+    want = replay(s, d, 1 << scale, reqs)
+    got = serve(s, d, 1 << scale, reqs, donation=1)  # every batch of >= 32 prefixes handed on
+    for i, (r, (c, h, ver)) in enumerate(zip(got, want)):
+        assert r["status"] == 0, (i, r)
+        assert (r["counts"], r["checksums"], r["version"]) == (c, h, ver), i
+
+
+def test_wave_wait_gives_up_as_a_request_error():
+    s, d = rmat_edges(10, seed=5)
+    n = 1 << 10
+    ctx = gj.Context(0)
+    q = gj.Query(ctx, *QUERIES["triangle"])
+    g = gj.Graph(ctx, s, d, n)
+    want = gj.count(g, q)
+    gj.set_tuning(ctx, wait_ms=50, fault=1)  # the queue waits on a warp that never finishes
+    srv = gj.Server(g)
+    r = srv.poll(srv.submit_count([q]))
+    assert r["status"] == -6  # GJ_E_TIMEOUT
+    srv.stop()
+    gj.set_tuning(ctx)
+    srv = gj.Server(g)
+    r = srv.poll(srv.submit_count([q]))
+    assert r["status"] == 0 and (r["counts"][0], r["checksums"][0]) == want
+    srv.stop()
+    ctx.close()
 
 
 def test_request_alone_equals_in_mix():
