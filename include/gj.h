@@ -58,7 +58,8 @@ enum {
     GJ_E_OVERFLOW = -7,   /* a match count passed 2^63 - 1 (the int64 result would wrap) */
     GJ_E_CUDA = -8,       /* a CUDA runtime call failed (gj_last_error has the text) */
     GJ_E_PENDING = -9,    /* request not finished yet */
-    GJ_E_NOTFOUND = -10   /* unknown request id */
+    GJ_E_NOTFOUND = -10,  /* unknown request id */
+    GJ_E_CHECK = -11      /* checked build only: a device bounds check failed (gj_last_error names it) */
 };
 
 typedef struct gj_ctx gj_ctx;
@@ -280,7 +281,10 @@ typedef struct {
      * a working warp that never finishes, so it can only end by its time bound
      * (the count call returns GJ_E_TIMEOUT; the context stays usable). 2: the
      * fused engine's per-query counts start at 2^63 - 1024, so a query with
-     * more than 1023 matches returns GJ_E_OVERFLOW. */
+     * more than 1023 matches returns GJ_E_OVERFLOW. 3 (checked build only,
+     * GJ_E_INVALID otherwise): the graph views the kernels get claim one
+     * vertex fewer than the graph has, so the first access to the last
+     * vertex's lists trips a bounds check and the call returns GJ_E_CHECK. */
     uint32_t fault;
 } gj_tuning;
 /* Copies the context's current settings to *out (fused_ms and plain_ms are
@@ -396,6 +400,14 @@ int gj_profile_enable(gj_ctx* ctx, int enabled);
 int gj_profile_read(gj_ctx* ctx, double* total_ms, uint64_t* launches);
 /* Number of kernels the library has launched on ctx since it was created. */
 uint64_t gj_launch_count(const gj_ctx* ctx);
+/* 1 in the checked build of the library (libgj_checks.so, compiled with
+ * GJ_CHECKS), 0 otherwise. The checked build guards every vertex id, list
+ * extent, edge slot, prefix-buffer slot and donated bundle its kernels
+ * use; a failed check skips the access (the kernel finishes) and the count,
+ * list or update call returns GJ_E_CHECK instead of its results (an update
+ * batch is then not committed). Served requests and gj_count_noalloc do not
+ * report checks; the next checked call on the context does. */
+int gj_checked_build(void);
 /* The cudaStream_t all launches of ctx go to. */
 void* gj_ctx_stream(gj_ctx* ctx);
 /* Waits for all work on ctx's stream. */

@@ -72,6 +72,24 @@ int gj_timer_collect(gj_ctx* ctx) {
     return GJ_OK;
 }
 
+int gj_check_status(gj_ctx* ctx) {
+    if (!GJ_CHECKED_BUILD) return GJ_OK;
+    unsigned long long* word = gj_check_word(ctx);
+    unsigned long long w = 0;
+    GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&w, word, sizeof(w), cudaMemcpyDeviceToHost, ctx->stream));
+    GJ_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!w) return GJ_OK;
+    GJ_CUDA_TRY(ctx, cudaMemsetAsync(word, 0, sizeof(w), ctx->stream));
+    static const char* const site[] = {"?", "vertex id", "list extent", "edge slot", "prefix-buffer slot",
+                                       "donated bundle"};
+    const unsigned s = (unsigned)(w >> 56);
+    char buf[160];
+    snprintf(buf, sizeof buf, "checked build: a %s bounds check failed (index %llu); the access was skipped",
+             site[s < 6 ? s : 0], (unsigned long long)(w & ((1ull << 56) - 1)));
+    gj_set_error(ctx, GJ_E_CHECK, buf);
+    return GJ_E_CHECK;
+}
+
 namespace {
 
 // 1: device memory of device dev, 0: host memory, -1: another device's memory
@@ -126,6 +144,7 @@ const char* gj_strerror(int code) {
         case GJ_E_CUDA: return "CUDA error";
         case GJ_E_PENDING: return "request pending";
         case GJ_E_NOTFOUND: return "unknown request";
+        case GJ_E_CHECK: return "a device bounds check failed (checked build)";
         default: return "unknown error";
     }
 }
@@ -163,6 +182,10 @@ int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
         gj_destroy(ctx);
         return GJ_E_NOMEM;
     }
+    if (cudaMemset(ctx->d_acc, 0, 64 * sizeof(uint64_t)) != cudaSuccess) {
+        gj_destroy(ctx);
+        return GJ_E_CUDA;
+    }
     *out = ctx;
     return GJ_OK;
 }
@@ -185,6 +208,8 @@ void gj_destroy(gj_ctx* ctx) {
 void* gj_ctx_stream(gj_ctx* ctx) { return ctx ? (void*)ctx->stream : nullptr; }
 
 uint64_t gj_launch_count(const gj_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int gj_checked_build(void) { return GJ_CHECKED_BUILD ? 1 : 0; }
 
 int gj_sync(gj_ctx* ctx) {
     if (!ctx) return GJ_E_INVALID;
@@ -227,6 +252,7 @@ int gj_graph_load_ex(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint
     *out = nullptr;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_RANGE("gj_graph_load (%llu edges)", (unsigned long long)m);
     cudaStream_t st = ctx->stream;
     const int ks = ptr_kind(src, ctx->device), kd = ptr_kind(dst, ctx->device);
     if (m > 0 && (ks < 0 || kd < 0)) {
@@ -300,6 +326,7 @@ int gj_graph_build_triangles(gj_graph* g, uint64_t* count) {
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_RANGE("gj_graph_build_triangles");
     GJ_TRY(gj_tri_build(ctx, g));
     if (count) *count = g->tri.count;
     return GJ_OK;
@@ -386,12 +413,14 @@ int gj_count_ex(gj_graph* g, const gj_query* q, uint32_t engine, uint32_t v_lo, 
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_RANGE("gj_count (k=%u, %s engine)", q->k, engine == GJ_ENGINE_PLAIN ? "level-synchronous" : "fused");
     GJ_TRY(ensure_tri(ctx, g, &q, 1));
     int rc;
     if (engine == GJ_ENGINE_PLAIN)
         rc = gj_engine_plain(ctx, g, q, v_lo, v_hi, count, checksum, nullptr, 0, nullptr);
     else
         rc = gj_engine_fused(ctx, g, &q, 1, v_lo, v_hi, count, checksum);
+    if (rc == GJ_OK) rc = gj_check_status(ctx);
     if (rc == GJ_OK && stats) *stats = ctx->work;
     return rc;
 }
@@ -405,8 +434,12 @@ int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32
     if (ctx->server) return GJ_E_INVALID;
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_RANGE("gj_count_many (%u queries, %s engine)", nq, engine == GJ_ENGINE_PLAIN ? "level-synchronous" : "fused");
     GJ_TRY(ensure_tri(ctx, g, qs, nq));
-    if (engine == GJ_ENGINE_FUSED) return gj_engine_fused(ctx, g, qs, nq, v_lo, v_hi, counts, checksums);
+    if (engine == GJ_ENGINE_FUSED) {
+        GJ_TRY(gj_engine_fused(ctx, g, qs, nq, v_lo, v_hi, counts, checksums));
+        return gj_check_status(ctx);
+    }
     gj_work_stats sum{};
     for (uint32_t i = 0; i < nq; i++) {
         GJ_TRY(gj_engine_plain(ctx, g, qs[i], v_lo, v_hi, counts + i, checksums + i, nullptr, 0, nullptr));
@@ -420,7 +453,7 @@ int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32
         }
     }
     ctx->work = sum;
-    return GJ_OK;
+    return gj_check_status(ctx);
 }
 
 int gj_count_many(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t engine, int64_t* counts,
@@ -443,7 +476,11 @@ int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out) {
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
     if (!ctx || !t || t->seed_chunk < 32 || t->seed_chunk > 4096 || t->seed_chunk % 32) return GJ_E_INVALID;
     if (t->prefix_buffer_bytes && t->prefix_buffer_bytes < (1ull << 20)) return GJ_E_INVALID;
-    if (t->donation > 2 || t->fault > GJ_FAULT_COUNT) return GJ_E_INVALID;
+    if (t->donation > 2 || t->fault > GJ_FAULT_NARROW_VIEW) return GJ_E_INVALID;
+    if (t->fault == GJ_FAULT_NARROW_VIEW && !GJ_CHECKED_BUILD) {
+        gj_set_error(ctx, GJ_E_INVALID, "failure injection 3 (narrowed graph views) needs the checked build");
+        return GJ_E_INVALID;
+    }
     ctx->seed_chunk = t->seed_chunk;
     ctx->wait_ms = t->wait_ms;
     ctx->fault = t->fault;
@@ -573,6 +610,7 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
         }
     DevSet ds(ctx->device);
     std::lock_guard<std::mutex> lk(ctx->mu);
+    GJ_RANGE("gj_apply_batch (%llu updates, %u queries)", (unsigned long long)b, nq);
     DeltaBuf buf;
     // the deltas go to the caller's arrays only once the batch is committed
     std::vector<int64_t> dc(nq);
@@ -583,6 +621,7 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
                                          dc.data(), dh.data());
     gj_work_stats sum = ctx->work;
     const uint64_t changes = buf.batch.n;
+    if (rc == GJ_OK) rc = gj_check_status(ctx);  // the batch is not committed after a failed check
     if (rc == GJ_OK) rc = gj_delta_commit(ctx, g, buf.batch);
     gj_delta_free(ctx, &buf);
     if (rc == GJ_OK) {
@@ -601,6 +640,7 @@ int gj_apply_batch(gj_graph* g, const uint32_t* src, const uint32_t* dst, const 
 
 int gj_delta_eval(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batch, const gj_query* const* qs, uint32_t nq,
                   uint32_t engine, int64_t* counts, uint64_t* checksums) {
+    GJ_RANGE("delta: evaluate %u delta queries (%s engine)", nq, engine == GJ_ENGINE_FUSED ? "fused" : "level-synchronous");
     for (uint32_t qi = 0; qi < nq; qi++) {
         counts[qi] = 0;
         checksums[qi] = 0;
@@ -667,6 +707,7 @@ int gj_list(gj_graph* g, const gj_query* q, uint32_t* out_tuples, uint64_t cap, 
     int64_t c = 0;
     uint64_t h = 0;
     GJ_TRY(gj_engine_plain(ctx, g, q, 0, UINT32_MAX, &c, &h, out_tuples, cap, written));
+    GJ_TRY(gj_check_status(ctx));
     *total = c;
     *checksum = h;
     return (uint64_t)c > cap ? GJ_E_TRUNCATED : GJ_OK;

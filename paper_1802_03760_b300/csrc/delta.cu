@@ -395,6 +395,7 @@ void gj_delta_free(gj_ctx* ctx, DeltaBuf* d) {
 
 int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const uint32_t* dst, const int8_t* sign,
                      uint64_t b, DeltaBuf* out) {
+    GJ_RANGE("delta: normalise batch");
     cudaStream_t st = ctx->stream;
     const uint64_t bb = b ? b : 1;
     // vertex -> range maps: at most nd distinct vertices per direction, 2x slots
@@ -672,6 +673,7 @@ int commit_side(gj_ctx* ctx, uint32_t n, const gj_csr& cur, uint64_t m, const De
 }  // namespace
 
 int gj_delta_commit(gj_ctx* ctx, gj_graph* g, const DeltaBatch& d, gj_csr* old_fwd, gj_csr* old_rev) {
+    GJ_RANGE("delta: commit (%llu changes)", (unsigned long long)d.n);
     cudaStream_t st = ctx->stream;
     if (d.n == 0) {
         g->version++;

@@ -331,11 +331,15 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             const BindList L = gj_bind_list(G, dir, v, tup[P.bpos2[j][b] * FC + i]);
                             len = L.len;
                             lp = L.p;
-                        } else {
+                        } else if (GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) {
                             const int64_t* off = dir ? G.ro : G.fo;
                             int64_t s = __ldg(off + v);
                             len = (uint64_t)(__ldg(off + v + 1) - s);
                             lp = (dir ? G.rn : G.fn) + s;
+                            if (!GJ_CHECK(G.chk, (uint64_t)s + len <= G.m, GJ_SITE_LIST, v)) len = 0;
+                        } else {
+                            len = 0;
+                            lp = G.fn;
                         }
                         if (len < best) {
                             best = len;
@@ -516,6 +520,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     k = P.k;
                 }
                 const uint32_t L = Bd.level, nb_ = Bd.n;
+                if (!GJ_CHECK(G.chk, nb_ <= FC && L >= 2 && L < k, GJ_SITE_BUNDLE, ((uint64_t)L << 32) | nb_)) {
+                    if (lane == 0) atomicExch(A.Q.seq + (took & mask), (unsigned long long)took + A.Q.cap);
+                    __syncwarp();
+                    continue;
+                }
                 uint32_t* tupL = reinterpret_cast<uint32_t*>(ws + off_tup(L, DELTA, EXT));
                 for (uint32_t c = 0; c < L; c++)
                     for (uint32_t i = lane; i < nb_; i += 32) tupL[c * FC + i] = Bd.tup[c][i];
@@ -876,8 +885,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     for (uint32_t b = 0; b < nb && keep; b++) {
                         if (b == b0) continue;
                         const uint32_t v = tup[P.bpos[j][b] * FC + i];
-                        keep = P.bdir[j][b] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
-                                            : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e);
+                        keep = GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v) &&
+                               (P.bdir[j][b] ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, e)
+                                             : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, e));
                     }
                 }
                 cur += 32;
@@ -901,7 +911,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     continue;
                 }
                 const uint32_t mask = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
+                if (keep && GJ_CHECK(G.chk, nn + __popc(mask & lt) < FC, GJ_SITE_PREFIX, nn + __popc(mask & lt))) {
                     const uint32_t slot = nn + __popc(mask & lt);
                     for (int p = 0; p < j; p++) nt[p * FC + slot] = tup[p * FC + i];
                     nt[j * FC + slot] = e;
@@ -1164,6 +1174,7 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
 int gj_engine_fused(gj_ctx* ctx, const gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32_t v_lo,
                     uint32_t v_hi, int64_t* counts, uint64_t* checksums) {
     if (nq == 0) return GJ_OK;
+    GJ_RANGE("fused launch (%u queries)", nq);
     cudaStream_t st = ctx->stream;
     if (v_hi > g->n) v_hi = g->n;
     if (v_lo > v_hi) v_lo = v_hi;

@@ -25,6 +25,7 @@ constexpr int PT = 256;  // threads per block
 struct Cols {
     uint32_t* x[GJ_MAX_K];
     int8_t* sg;  // sign of the seed each prefix descends from (delta queries)
+    uint64_t cap;  // slots of each column
 };
 
 struct Acc {
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(PT) k_seed(Plan P, GraphView G, DeltaView D, D
         unsigned long long b0 = 0;
         if (lane == leader) b0 = atomicAdd(acc.n_out, (unsigned long long)__popc(mask));
         b0 = __shfl_sync(0xffffffffu, b0, leader);
-        if (keep) {
+        if (keep && GJ_CHECK(G.chk, b0 + __popc(mask & lt) < out.cap, GJ_SITE_PREFIX, b0 + __popc(mask & lt))) {
             uint64_t s = b0 + __popc(mask & lt);
             out.x[0][s] = x0;
             out.x[1][s] = x1;
@@ -172,13 +173,19 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, DeltaView D,
             const uint32_t b = mini[i];
             for (uint32_t p = 0; p < j; p++) xs[p] = in.x[p][i];
             if (in.sg) sign = in.sg[i];
-            uint32_t e;
+            uint32_t e = 0;
             if (P.bdir[j][b] == GJ_BIND_TRI) {
-                e = __ldg(gj_bind_list(G, GJ_BIND_TRI, xs[P.bpos[j][b]], xs[P.bpos2[j][b]]).p + r);
+                const BindList L = gj_bind_list(G, GJ_BIND_TRI, xs[P.bpos[j][b]], xs[P.bpos2[j][b]]);
+                if (GJ_CHECK(G.chk, r < L.len, GJ_SITE_LIST, r)) e = __ldg(L.p + r);
+                else keep = false;
             } else {
                 const ViewList L = gj_view_list(G, Dv, P.bdir[j][b], P.bview[j][b], xs[P.bpos[j][b]]);
-                e = r < L.base_len ? __ldg(L.base + r) : __ldg(L.ins + (r - L.base_len));
-                if (r < L.base_len && L.ndel) keep = !gj_contains(L.del, L.ndel, e);  // deleted in the new version
+                if (GJ_CHECK(G.chk, r < L.space(), GJ_SITE_LIST, r)) {
+                    e = r < L.base_len ? __ldg(L.base + r) : __ldg(L.ins + (r - L.base_len));
+                    if (r < L.base_len && L.ndel) keep = !gj_contains(L.del, L.ndel, e);  // deleted in the new version
+                } else {
+                    keep = false;
+                }
             }
             xs[j] = e;
             for (uint32_t bb = 0; bb < P.nb[j] && keep; bb++) {
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(PT) k_extend(Plan P, GraphView G, DeltaView D,
         unsigned long long b0 = 0;
         if (lane == leader) b0 = atomicAdd(acc.n_out, (unsigned long long)__popc(mask));
         b0 = __shfl_sync(0xffffffffu, b0, leader);
-        if (keep) {
+        if (keep && GJ_CHECK(G.chk, b0 + __popc(mask & lt) < out.cap, GJ_SITE_PREFIX, b0 + __popc(mask & lt))) {
             uint64_t s = b0 + __popc(mask & lt);
             for (uint32_t p = 0; p <= j; p++) out.x[p][s] = xs[p];
             if (out.sg) out.sg[s] = (int8_t)sign;
@@ -279,6 +286,7 @@ int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t
         for (uint32_t j = 2; j < k; j++) {
             for (uint32_t p = 0; p < j; p++) L[j].cols.x[p] = (uint32_t*)take(4 * capacity);
             L[j].cols.sg = P.delta ? (int8_t*)take(capacity) : nullptr;
+            L[j].cols.cap = capacity;
             L[j].cnt = (uint32_t*)take(4 * capacity);
             L[j].mini = (uint8_t*)take(capacity);
             L[j].coff = (int64_t*)take(8 * (capacity + 1));
@@ -301,6 +309,7 @@ int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t
     };
     // count, scan and read back the candidate total of level j
     auto prepare = [&](uint32_t j) -> int {
+        GJ_RANGE("level %u: count", j);
         Level& l = L[j];
         l.cursor = 0;
         l.total = 0;
@@ -335,6 +344,7 @@ int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t
                 if (seed_cursor >= se[1]) break;
                 int64_t chunk = se[1] - seed_cursor;
                 if ((uint64_t)chunk > capacity) chunk = (int64_t)capacity;
+                GJ_RANGE("level 2: seeds");
                 GJ_CUDA_TRY(ctx, cudaMemsetAsync(A.n_out, 0, 8, st));
                 k_seed<<<grid, PT, 0, st>>>(P, G, D, B, seed_cursor, seed_cursor + chunk, L[2].cols, A, 0, nullptr,
                                             0);
@@ -347,6 +357,7 @@ int gj_engine_plain_plan(gj_ctx* ctx, const gj_graph* g, const Plan& P, uint32_t
                 continue;
             }
             Level& l = L[jd];
+            GJ_RANGE("level %d: propose and intersect", jd);
             if (jd == (int)k - 1) {
                 gj_timer_begin(ctx);
                 k_extend<<<grid, PT, 0, st>>>(P, G, D, jd, l.cols, l.n, l.coff, l.mini, l.cursor, l.total, 1, Cols{},

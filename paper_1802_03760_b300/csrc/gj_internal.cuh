@@ -8,6 +8,8 @@
 #include <climits>
 #include <vector>
 #include <mutex>
+#include <cstdio>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/gj.h"
 
@@ -80,7 +82,31 @@ struct GraphView {
     const uint32_t* __restrict__ tt;
     const uint4* __restrict__ em;     // edge (a, b) -> its forward slot: {a, b, slot, 0}, 2^ebits entries
     uint32_t ebits;
+    uint64_t tcount = 0;               // entries of the triangle lists
+    unsigned long long* chk = nullptr;  // checked build: the bounds-check word (see GJ_CHECK)
 };
+
+// Bounds checks of the checked build (compiled with -DGJ_CHECKS). Each
+// guards one access: a vertex id against the view's vertex count, a list's
+// extent against its array, an edge slot against the edge count, a
+// prefix-buffer slot against the buffer, a donated bundle's size and level.
+// A failed check records (site << 56 | index) in the word chk once and
+// makes the guarded access a no-op (an empty list, a non-member, a dropped
+// prefix), so the kernel runs to its end; the API call then returns
+// GJ_E_CHECK. In the normal build GJ_CHECK is the constant true and the
+// condition is not evaluated.
+enum { GJ_SITE_VERTEX = 1, GJ_SITE_LIST = 2, GJ_SITE_EDGE = 3, GJ_SITE_PREFIX = 4, GJ_SITE_BUNDLE = 5 };
+#ifdef GJ_CHECKS
+constexpr bool GJ_CHECKED_BUILD = true;
+__device__ __forceinline__ bool gj_check(unsigned long long* w, bool ok, uint32_t site, uint64_t idx) {
+    if (!ok && w) atomicCAS(w, 0ull, ((unsigned long long)site << 56) | (idx & ((1ull << 56) - 1)));
+    return ok;
+}
+#define GJ_CHECK(w, cond, site, idx) gj_check((w), (cond), (site), (uint64_t)(idx))
+#else
+constexpr bool GJ_CHECKED_BUILD = false;
+#define GJ_CHECK(w, cond, site, idx) true
+#endif
 
 // The ternary relation tri(a, b, c) (a -> b, a -> c, b -> c; Section 5.4)
 // indexed by its first two attributes: for the forward slot e of the edge
@@ -109,11 +135,7 @@ struct gj_graph {
     gj_csr spare_fwd, spare_rev;  // the previous version's arrays, reused by the next update's commit
     uint32_t* relabel = nullptr;  // new id of each input id (degree renaming), null = identity
     uint32_t load_flags = 0;
-    GraphView view() const {
-        return GraphView{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
-                         fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr, tri.tab_off, tri.tab,
-                         tri.emap, tri.ebits};
-    }
+    GraphView view() const;  // the arrays the kernels read (defined after gj_ctx)
 };
 
 // ------------------------------------------------------------------ plan
@@ -254,8 +276,31 @@ struct gj_ctx {
 
 // Failure injection (gj_tuning.fault): the fused engine's end-of-launch wait
 // misses one warp (it ends by its time bound), or its counts start just
-// below 2^63 (they overflow).
-enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2 };
+// below 2^63 (they overflow), or (checked build only) the graph views the
+// kernels get claim one vertex fewer than the graph has, so that the first
+// access to the last vertex trips the vertex bounds check.
+enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2, GJ_FAULT_NARROW_VIEW = 3 };
+
+// The bounds-check word of the checked build: the last word of the
+// context's accumulators, which no engine clears.
+inline unsigned long long* gj_check_word(const gj_ctx* ctx) {
+    return GJ_CHECKED_BUILD ? reinterpret_cast<unsigned long long*>(ctx->d_acc + 63) : nullptr;
+}
+
+inline GraphView gj_graph::view() const {
+    GraphView v{n, m, fwd.off, fwd.nbr, fwd.key, rev.off, rev.nbr, rev.key,
+                fwd.tab_off, fwd.tab, rev.tab_off, rev.tab, tri.off, tri.nbr, tri.tab_off, tri.tab,
+                tri.emap, tri.ebits};
+    v.tcount = tri.count;
+    v.chk = gj_check_word(ctx);
+    if (GJ_CHECKED_BUILD && ctx->fault == GJ_FAULT_NARROW_VIEW && v.n > 0) v.n--;
+    return v;
+}
+
+// Checked build: GJ_E_CHECK (with the site and index in the context's
+// error text) if a bounds check failed since the last call, and the word
+// cleared; GJ_OK otherwise. The normal build returns GJ_OK at once.
+int gj_check_status(gj_ctx* ctx);
 
 // Engine of a batch's delta queries: the level-synchronous one spreads a
 // small batch's fan-out over the whole GPU at once, the fused one balances
@@ -271,6 +316,28 @@ inline uint64_t gj_wait_ns(const gj_ctx* ctx) { return (uint64_t)(ctx->wait_ms ?
 
 // Counts one kernel launch of ctx (gj_launch_count reports the total).
 #define GJ_LAUNCHED(ctx) ((ctx)->launches++)
+
+// NVTX range over a scope (host-side: the API call, a level step of the
+// level-synchronous engine, a served wave or batch); it costs nothing
+// unless a profiler is attached. The name may be printf-formatted.
+struct GjRange {
+    template <typename... T>
+    explicit GjRange(const char* fmt, T... args) {
+        if constexpr (sizeof...(T) == 0) {
+            nvtxRangePushA(fmt);
+        } else {
+            char buf[96];
+            snprintf(buf, sizeof buf, fmt, args...);
+            nvtxRangePushA(buf);
+        }
+    }
+    ~GjRange() { nvtxRangePop(); }
+    GjRange(const GjRange&) = delete;
+    GjRange& operator=(const GjRange&) = delete;
+};
+#define GJ_CAT2(a, b) a##b
+#define GJ_CAT(a, b) GJ_CAT2(a, b)
+#define GJ_RANGE(...) GjRange GJ_CAT(gj_range_, __LINE__)(__VA_ARGS__)
 
 // Grow-only device scratch buffer `slot` of at least `bytes`.
 int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out);
@@ -488,9 +555,11 @@ __device__ __forceinline__ uint4 gj_delta_ranges(const DeltaSide& S, uint32_t v)
 
 __device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
                                                  uint32_t v) {
+    if (!GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) return ViewList{G.fn, 0, nullptr, 0, nullptr, 0};
     const int64_t* off = dir ? G.ro : G.fo;
     const int64_t s = __ldg(off + v);
     ViewList L{(dir ? G.rn : G.fn) + s, (uint32_t)(__ldg(off + v + 1) - s), nullptr, 0, nullptr, 0};
+    if (!GJ_CHECK(G.chk, (uint64_t)s + L.base_len <= G.m, GJ_SITE_LIST, v)) L.base_len = 0;
     if (view == GJ_VIEW_NEW && D) {
         const DeltaSide& S = dir ? D->rev : D->fwd;
         const uint4 r = gj_delta_ranges(S, v);
@@ -507,6 +576,7 @@ __device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const Delta
 // deletes present), then the committed index.
 __device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
                                                uint32_t v, uint32_t x) {
+    if (!GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) return false;
     if (view == GJ_VIEW_NEW && D) {
         const DeltaSide& S = dir ? D->rev : D->fwd;
         const uint4 r = gj_delta_ranges(S, v);
@@ -549,15 +619,18 @@ __device__ __forceinline__ BindList gj_bind_list(const GraphView& G, uint32_t di
     if (dir == GJ_BIND_TRI) {
         // the triangles on the edge v -> v2: its forward slot, then its list
         const int64_t e = gj_edge_slot(G, v, v2);
-        if (e < 0) return BindList{G.fn, 0u, nullptr, 0u};
+        if (e < 0 || !GJ_CHECK(G.chk, (uint64_t)e < G.m, GJ_SITE_EDGE, e)) return BindList{G.fn, 0u, nullptr, 0u};
         const int64_t a = __ldg(G.to + e);
         const uint32_t len = (uint32_t)(__ldg(G.to + e + 1) - a);
+        if (!GJ_CHECK(G.chk, (uint64_t)a + len <= G.tcount, GJ_SITE_LIST, e)) return BindList{G.fn, 0u, nullptr, 0u};
         if (len >= GJ_HASH_MIN_DEG) return BindList{G.tn + a, len, G.tt + __ldg(G.tto + e), gj_tab_bits(len)};
         return BindList{G.tn + a, len, nullptr, 0u};
     }
+    if (!GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) return BindList{G.fn, 0u, nullptr, 0u};
     const int64_t* off = dir ? G.ro : G.fo;
     const int64_t s = __ldg(off + v);
     const uint32_t len = (uint32_t)(__ldg(off + v + 1) - s);
+    if (!GJ_CHECK(G.chk, (uint64_t)s + len <= G.m, GJ_SITE_LIST, v)) return BindList{G.fn, 0u, nullptr, 0u};
     const uint32_t* p = (dir ? G.rn : G.fn) + s;
     if (len >= GJ_HASH_MIN_DEG) return BindList{p, len, (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v), gj_tab_bits(len)};
     return BindList{p, len, nullptr, 0u};

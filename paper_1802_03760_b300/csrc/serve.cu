@@ -185,6 +185,7 @@ bool launch_wave(gj_server* S) {
             for (const gj_query* q : r->qs) plans.push_back(q->plan);
         }
     }
+    GJ_RANGE("serve: wave of %zu requests", take.size());
     Wave* w = new Wave();
     w->reqs = take;
     w->nq = (uint32_t)plans.size();
@@ -245,6 +246,7 @@ bool run_batch(gj_server* S) {
     gj_ctx* ctx = S->ctx;
     gj_graph* g = S->g;
     const uint32_t nq = (uint32_t)r->qs.size();
+    GJ_RANGE("serve: update batch of %zu", r->src.size());
     std::vector<int64_t> c(nq, 0);
     std::vector<uint64_t> h(nq, 0);
     DeltaBuf buf;

@@ -3,7 +3,9 @@
 Every step of the evaluation runs in the CUDA library; this module converts
 numpy arrays, torch tensors and Python lists to pointers and raises on error
 codes. If ``libgj.so`` has not been built it raises instead of falling back
-to anything else.
+to anything else. With the environment variable GJ_CHECKS=1 it loads the
+checked build ``libgj_checks.so`` instead (device bounds checks that return
+GJ_E_CHECK).
 """
 from __future__ import annotations
 
@@ -15,7 +17,7 @@ import weakref
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgj.so")
+LIB_PATH = os.path.join(_HERE, "libgj_checks.so" if os.environ.get("GJ_CHECKS") == "1" else "libgj.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "gj.h")
 
 ENGINE_PLAIN = 0
@@ -125,6 +127,7 @@ _SIGS = {
     "gj_profile_read": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _U64P]),
     "gj_ctx_stream": (_VP, [_VP]),
     "gj_launch_count": (ctypes.c_uint64, [_VP]),
+    "gj_checked_build": (ctypes.c_int, []),
     "gj_sync": (ctypes.c_int, [_VP]),
 }
 
@@ -141,7 +144,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libgj.so is not built; run `python -m paper_1802_03760_b300.build` "
+            raise ImportError(os.path.basename(LIB_PATH) + " is not built; run `python -m paper_1802_03760_b300.build` "
                               "(there is no fallback implementation)")
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
@@ -366,6 +369,11 @@ def get_tuning(ctx: Context) -> dict:
     t = Tuning()
     _check(lib().gj_get_tuning(ctx._h, ctypes.byref(t)), ctx)
     return t.as_dict()
+
+
+def checked_build() -> bool:
+    """Whether the loaded library is the checked build (GJ_CHECKS=1)."""
+    return bool(lib().gj_checked_build())
 
 
 def set_tuning(ctx: Context, seed_chunk: int = 32, blocks_per_sm: int = 0, prefix_buffer_bytes: int = 0,

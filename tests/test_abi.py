@@ -17,6 +17,20 @@ def test_library_builds_and_exports_header_symbols():
         assert hasattr(L, n), n
 
 
+def test_checked_build_exports_header_symbols():
+    """libgj_checks.so (the same sources compiled with GJ_CHECKS) exports the
+    same entry points and says it is the checked build; the normal build
+    says it is not, and refuses the checked build's failure injection."""
+    from paper_1802_03760_b300.build import LIB_CHECKS
+    build()
+    C = ctypes.CDLL(LIB_CHECKS)
+    for n in gj.header_functions():
+        assert hasattr(C, n), n
+    assert C.gj_checked_build() == 1
+    assert gj.lib().gj_checked_build() == 0
+    assert gj.lib().gj_strerror(-11) == b"a device bounds check failed (checked build)"
+
+
 def test_binding_covers_header():
     assert sorted(gj._SIGS) == gj.header_functions()
 
