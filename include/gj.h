@@ -59,7 +59,8 @@ enum {
     GJ_E_CUDA = -8,       /* a CUDA runtime call failed (gj_last_error has the text) */
     GJ_E_PENDING = -9,    /* request not finished yet */
     GJ_E_NOTFOUND = -10,  /* unknown request id */
-    GJ_E_CHECK = -11      /* checked build only: a device bounds check failed (gj_last_error names it) */
+    GJ_E_CHECK = -11,     /* checked build only: a device bounds check failed (gj_last_error names it) */
+    GJ_E_CANCELLED = -12  /* the request was withdrawn by gj_cancel before it started */
 };
 
 typedef struct gj_ctx gj_ctx;
@@ -284,8 +285,13 @@ typedef struct {
      * more than 1023 matches returns GJ_E_OVERFLOW. 3 (checked build only,
      * GJ_E_INVALID otherwise): the graph views the kernels get claim one
      * vertex fewer than the graph has, so the first access to the last
-     * vertex's lists trips a bounds check and the call returns GJ_E_CHECK. */
+     * vertex's lists trips a bounds check and the call returns GJ_E_CHECK.
+     * 4: the library's device allocations after the first fault_count
+     * (counted from this setting) fail as if the device were out of memory:
+     * the call returns GJ_E_NOMEM and leaves the graph as it was (a failed
+     * load creates no graph, a failed update batch commits nothing). */
     uint32_t fault;
+    uint32_t fault_count;
 } gj_tuning;
 /* Copies the context's current settings to *out (fused_ms and plain_ms are
  * 0: only gj_autotune's output carries them). Errors: GJ_E_INVALID (null pointer). */
@@ -388,6 +394,12 @@ int gj_submit_count(gj_ctx* ctx, const gj_query* const* qs, uint32_t nq, uint64_
  * the nq <= 64 queries whose deltas it reports (see gj_apply_batch). */
 int gj_submit_batch(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, const int8_t* sign, uint64_t b,
                     const gj_query* const* qs, uint32_t nq, uint64_t* req_id);
+/* Withdraws a request that has not started: GJ_OK, and the request is
+ * finished with status GJ_E_CANCELLED (collect it with gj_poll). A cancelled
+ * update batch is never applied: later requests see the graph without it.
+ * GJ_E_PENDING if the request has started or finished (it keeps its
+ * result), GJ_E_NOTFOUND for an unknown or retired id. */
+int gj_cancel(gj_ctx* ctx, uint64_t req_id);
 /* Waits up to wait_ms (-1: without limit, 0: not at all) for a request; on
  * GJ_OK *out holds its result and the request is retired. GJ_E_PENDING if
  * it is still running, GJ_E_NOTFOUND for an unknown or retired id. */

@@ -10,6 +10,26 @@ void gj_set_error(gj_ctx* ctx, int code, const std::string& msg) {
     if (ctx) ctx->last_error = msg;
 }
 
+static bool alloc_injected(gj_ctx* ctx) {
+    return ctx && ctx->fault == GJ_FAULT_ALLOC && ctx->allocs.fetch_add(1) >= ctx->fault_count;
+}
+
+cudaError_t gj_malloc(gj_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (alloc_injected(ctx)) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
+cudaError_t gj_malloc_async(gj_ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (alloc_injected(ctx)) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e != cudaSuccess) *p = nullptr;
+    return e;
+}
+
 int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out) {
     ScratchArena& a = ctx->scratch[slot];
     if (a.bytes < bytes) {
@@ -20,7 +40,7 @@ int gj_scratch(gj_ctx* ctx, int slot, size_t bytes, void** out) {
             a.bytes = 0;
         }
         size_t want = bytes + bytes / 8;
-        GJ_CUDA_TRY(ctx, cudaMalloc(&a.ptr, want));
+        GJ_CUDA_TRY(ctx, gj_malloc(ctx, &a.ptr, want));
         a.bytes = want;
     }
     *out = a.ptr;
@@ -145,6 +165,7 @@ const char* gj_strerror(int code) {
         case GJ_E_PENDING: return "request pending";
         case GJ_E_NOTFOUND: return "unknown request";
         case GJ_E_CHECK: return "a device bounds check failed (checked build)";
+        case GJ_E_CANCELLED: return "request cancelled";
         default: return "unknown error";
     }
 }
@@ -177,7 +198,7 @@ int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
         }
         ctx->own_stream = true;
     }
-    if (cudaMalloc(&ctx->d_acc, 64 * sizeof(uint64_t)) != cudaSuccess ||
+    if (gj_malloc(ctx, &ctx->d_acc, 64 * sizeof(uint64_t)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_acc, 64 * sizeof(uint64_t)) != cudaSuccess) {
         gj_destroy(ctx);
         return GJ_E_NOMEM;
@@ -265,7 +286,7 @@ int gj_graph_load_ex(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, uint
     const uint32_t* dd_ = dst;
     uint32_t* tmp = nullptr;
     if (m > 0 && (sym || ks == 0 || kd == 0)) {
-        GJ_CUDA_TRY(ctx, cudaMallocAsync(&tmp, 2 * mm * sizeof(uint32_t), st));
+        GJ_CUDA_TRY(ctx, gj_malloc_async(ctx, &tmp, 2 * mm * sizeof(uint32_t), st));
         cudaError_t e = cudaSuccess;
         ds_ = tmp;
         dd_ = tmp + mm;
@@ -470,13 +491,14 @@ int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out) {
     out->donation = ctx->donation;
     out->wait_ms = ctx->wait_ms;
     out->fault = ctx->fault;
+    out->fault_count = ctx->fault_count;
     return GJ_OK;
 }
 
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
     if (!ctx || !t || t->seed_chunk < 32 || t->seed_chunk > 4096 || t->seed_chunk % 32) return GJ_E_INVALID;
     if (t->prefix_buffer_bytes && t->prefix_buffer_bytes < (1ull << 20)) return GJ_E_INVALID;
-    if (t->donation > 2 || t->fault > GJ_FAULT_NARROW_VIEW) return GJ_E_INVALID;
+    if (t->donation > 2 || t->fault > GJ_FAULT_ALLOC) return GJ_E_INVALID;
     if (t->fault == GJ_FAULT_NARROW_VIEW && !GJ_CHECKED_BUILD) {
         gj_set_error(ctx, GJ_E_INVALID, "failure injection 3 (narrowed graph views) needs the checked build");
         return GJ_E_INVALID;
@@ -484,6 +506,8 @@ int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
     ctx->seed_chunk = t->seed_chunk;
     ctx->wait_ms = t->wait_ms;
     ctx->fault = t->fault;
+    ctx->fault_count = t->fault_count;
+    ctx->allocs = 0;
     ctx->donation = t->donation;
     ctx->blocks_per_sm = t->blocks_per_sm;
     ctx->opt.prefix_buffer_bytes = t->prefix_buffer_bytes;

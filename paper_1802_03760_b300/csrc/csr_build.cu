@@ -129,9 +129,9 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
     int64_t mu = 0;
     GJ_CUDA_TRY(ctx, cudaMemcpyAsync(&mu, pos + m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     GJ_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    GJ_CUDA_TRY(ctx, cudaMalloc(&out->off, sizeof(int64_t) * ((size_t)n + 1)));
-    GJ_CUDA_TRY(ctx, cudaMalloc(&out->nbr, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
-    GJ_CUDA_TRY(ctx, cudaMalloc(&out->key, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->off, sizeof(int64_t) * ((size_t)n + 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->nbr, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->key, sizeof(uint32_t) * (size_t)(mu ? mu : 1)));
     out->cap_m = (uint64_t)(mu ? mu : 1);
     if (m > 0) {
         k_scatter_unique<<<grid_for(ctx, m), 256, 0, st>>>(sorted, m, flag, pos, vb, out->nbr, out->key);
@@ -146,14 +146,14 @@ int build_index(gj_ctx* ctx, const uint32_t* hi, const uint32_t* lo, uint64_t m,
 
 int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out) {
     cudaStream_t st = ctx->stream;
-    if (!out->off) GJ_CUDA_TRY(ctx, cudaMalloc(&out->off, sizeof(int64_t) * ((size_t)n + 1)));
+    if (!out->off) GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->off, sizeof(int64_t) * ((size_t)n + 1)));
     k_offsets<<<grid_for(ctx, (uint64_t)n + 1), 256, 0, st>>>(out->key, mu, n, out->off);
     GJ_LAUNCHED(ctx);
     GJ_CUDA_TRY(ctx, cudaGetLastError());
     // hash sets of the long lists
     int64_t* size = nullptr;
-    GJ_CUDA_TRY(ctx, cudaMallocAsync(&size, sizeof(int64_t) * ((size_t)n + 1), st));
-    GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab_off, sizeof(int64_t) * ((size_t)n + 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc_async(ctx, &size, sizeof(int64_t) * ((size_t)n + 1), st));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->tab_off, sizeof(int64_t) * ((size_t)n + 1)));
     k_tab_sizes<<<grid_for(ctx, n), 256, 0, st>>>(out->off, n, size);
     GJ_LAUNCHED(ctx);
     int rc = gj_scan_i64(ctx, size, out->tab_off, n);
@@ -164,7 +164,7 @@ int gj_csr_finish(gj_ctx* ctx, uint32_t n, uint64_t mu, gj_csr* out) {
     }
     cudaFreeAsync(size, st);
     GJ_TRY(rc);
-    GJ_CUDA_TRY(ctx, cudaMalloc(&out->tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &out->tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
     out->cap_tab = (uint64_t)(tsz ? tsz : 1);
     if (tsz > 0) {
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(out->tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
@@ -188,10 +188,10 @@ int gj_csr_build(gj_ctx* ctx, const uint32_t* d_src, const uint32_t* d_dst, uint
         return e == cudaErrorMemoryAllocation ? GJ_E_NOMEM : GJ_E_CUDA;
     };
     cudaError_t e;
-    if ((e = cudaMallocAsync(&keys, mm * 8, st)) != cudaSuccess) return fail(e);
-    if ((e = cudaMallocAsync(&keys2, mm * 8, st)) != cudaSuccess) { cudaFreeAsync(keys, st); return fail(e); }
-    if ((e = cudaMallocAsync(&flag, mm * 4, st)) != cudaSuccess) { cudaFreeAsync(keys, st); cudaFreeAsync(keys2, st); return fail(e); }
-    if ((e = cudaMallocAsync(&pos, (mm + 1) * 8 + 64, st)) != cudaSuccess) {
+    if ((e = gj_malloc_async(ctx, &keys, mm * 8, st)) != cudaSuccess) return fail(e);
+    if ((e = gj_malloc_async(ctx, &keys2, mm * 8, st)) != cudaSuccess) { cudaFreeAsync(keys, st); return fail(e); }
+    if ((e = gj_malloc_async(ctx, &flag, mm * 4, st)) != cudaSuccess) { cudaFreeAsync(keys, st); cudaFreeAsync(keys2, st); return fail(e); }
+    if ((e = gj_malloc_async(ctx, &pos, (mm + 1) * 8 + 64, st)) != cudaSuccess) {
         cudaFreeAsync(keys, st); cudaFreeAsync(keys2, st); cudaFreeAsync(flag, st); return fail(e);
     }
     err = (uint32_t*)(pos + mm + 1);

@@ -408,7 +408,7 @@ int gj_delta_prepare(gj_ctx* ctx, const gj_graph* g, const uint32_t* src, const 
         gj_set_error(ctx, GJ_E_INVALID, "update batch: an input array is in another device's memory");
         return GJ_E_INVALID;
     }
-    GJ_CUDA_TRY(ctx, cudaMallocAsync(&out->mem, bytes, st));
+    GJ_CUDA_TRY(ctx, gj_malloc_async(ctx, &out->mem, bytes, st));
     Arena A{(char*)out->mem, 0, bytes};
     const uint32_t* d_src = src;
     const uint32_t* d_dst = dst;
@@ -552,16 +552,16 @@ namespace {
 // Arrays of c sized for n vertices, m slots and t hash-set slots, reusing
 // those it has (a spare index) when they are large enough.
 int ensure_csr(gj_ctx* ctx, gj_csr& c, uint32_t n, uint64_t m, uint64_t t) {
-    if (!c.off) GJ_CUDA_TRY(ctx, cudaMalloc(&c.off, sizeof(int64_t) * ((size_t)n + 1)));
-    if (!c.tab_off) GJ_CUDA_TRY(ctx, cudaMalloc(&c.tab_off, sizeof(int64_t) * ((size_t)n + 1)));
+    if (!c.off) GJ_CUDA_TRY(ctx, gj_malloc(ctx, &c.off, sizeof(int64_t) * ((size_t)n + 1)));
+    if (!c.tab_off) GJ_CUDA_TRY(ctx, gj_malloc(ctx, &c.tab_off, sizeof(int64_t) * ((size_t)n + 1)));
     if (c.cap_m < (m ? m : 1)) {
         if (c.nbr) cudaFree(c.nbr);
         if (c.key) cudaFree(c.key);
         c.nbr = c.key = nullptr;
         c.cap_m = 0;
         const uint64_t cap = m + m / 16 + 1024;  // room for the growth of later updates
-        GJ_CUDA_TRY(ctx, cudaMalloc(&c.nbr, sizeof(uint32_t) * cap));
-        GJ_CUDA_TRY(ctx, cudaMalloc(&c.key, sizeof(uint32_t) * cap));
+        GJ_CUDA_TRY(ctx, gj_malloc(ctx, &c.nbr, sizeof(uint32_t) * cap));
+        GJ_CUDA_TRY(ctx, gj_malloc(ctx, &c.key, sizeof(uint32_t) * cap));
         c.cap_m = cap;
     }
     if (c.cap_tab < (t ? t : 1)) {
@@ -569,7 +569,7 @@ int ensure_csr(gj_ctx* ctx, gj_csr& c, uint32_t n, uint64_t m, uint64_t t) {
         c.tab = nullptr;
         c.cap_tab = 0;
         const uint64_t cap = t + t / 16 + 1024;
-        GJ_CUDA_TRY(ctx, cudaMalloc(&c.tab, sizeof(uint32_t) * cap));
+        GJ_CUDA_TRY(ctx, gj_malloc(ctx, &c.tab, sizeof(uint32_t) * cap));
         c.cap_tab = cap;
     }
     return GJ_OK;
@@ -590,7 +590,7 @@ int commit_side(gj_ctx* ctx, uint32_t n, const gj_csr& cur, uint64_t m, const De
     // ST, olen, OLP, nlen, NLP, ntab, NTP; every piece starts on a 256-byte boundary
     const size_t bytes = 16 * nk + 4 * nk + 4 * nk + 11 * 8 * (nk + 1) + 14 * 256;
     char* mem = nullptr;
-    GJ_CUDA_TRY(ctx, cudaMallocAsync(&mem, bytes, st));
+    GJ_CUDA_TRY(ctx, gj_malloc_async(ctx, &mem, bytes, st));
     Arena A{mem, 0, bytes};
     uint64_t* keys = (uint64_t*)A.take(16 * nk);
     uint32_t* flag = (uint32_t*)A.take(4 * nk);

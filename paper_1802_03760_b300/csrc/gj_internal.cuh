@@ -8,6 +8,7 @@
 #include <climits>
 #include <vector>
 #include <mutex>
+#include <atomic>
 #include <cstdio>
 #include <nvtx3/nvToolsExt.h>
 
@@ -272,6 +273,8 @@ struct gj_ctx {
     uint32_t donation = 0;       // fused engine work donation: 0 when warps idle, 1 always, 2 off
     uint32_t wait_ms = 0;        // bound of the fused engine's end-of-launch wait without progress, 0 = 10 s
     uint32_t fault = 0;          // failure injection for tests (GJ_FAULT_*)
+    uint32_t fault_count = 0;    // GJ_FAULT_ALLOC: allocations that still succeed
+    std::atomic<uint64_t> allocs{0};  // device allocations since the settings were applied
 };
 
 // Failure injection (gj_tuning.fault): the fused engine's end-of-launch wait
@@ -279,7 +282,21 @@ struct gj_ctx {
 // below 2^63 (they overflow), or (checked build only) the graph views the
 // kernels get claim one vertex fewer than the graph has, so that the first
 // access to the last vertex trips the vertex bounds check.
-enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2, GJ_FAULT_NARROW_VIEW = 3 };
+enum { GJ_FAULT_NONE = 0, GJ_FAULT_WAIT = 1, GJ_FAULT_COUNT = 2, GJ_FAULT_NARROW_VIEW = 3, GJ_FAULT_ALLOC = 4 };
+
+// Every device allocation of the library goes through these two, so that
+// failure injection 4 can make the allocations after the first fault_count
+// fail (as cudaErrorMemoryAllocation). On failure *p is null.
+cudaError_t gj_malloc(gj_ctx* ctx, void** p, size_t bytes);
+cudaError_t gj_malloc_async(gj_ctx* ctx, void** p, size_t bytes, cudaStream_t st);
+template <typename T>
+inline cudaError_t gj_malloc(gj_ctx* ctx, T** p, size_t bytes) {
+    return gj_malloc(ctx, reinterpret_cast<void**>(p), bytes);
+}
+template <typename T>
+inline cudaError_t gj_malloc_async(gj_ctx* ctx, T** p, size_t bytes, cudaStream_t st) {
+    return gj_malloc_async(ctx, reinterpret_cast<void**>(p), bytes, st);
+}
 
 // The bounds-check word of the checked build: the last word of the
 // context's accumulators, which no engine clears.

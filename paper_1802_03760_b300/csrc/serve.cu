@@ -12,6 +12,8 @@
 // versions it would see if the requests ran one by one in submission order.
 // Requests are admitted against a device-memory budget; a request that can
 // never fit is failed with GJ_E_ADMIT.
+#include <algorithm>
+
 #include "gj_internal.cuh"
 
 #include <chrono>
@@ -193,7 +195,7 @@ bool launch_wave(gj_server* S) {
     w->version = S->g->version;
     gj_ctx* ctx = S->ctx;
     int rc = GJ_OK;
-    if (cudaMallocAsync(&w->dscratch, w->mem, S->s_count) != cudaSuccess ||
+    if (gj_malloc_async(ctx, &w->dscratch, w->mem, S->s_count) != cudaSuccess ||
         cudaMallocHost(&w->hres, 16 * (size_t)w->nq + 16) != cudaSuccess ||
         cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -418,6 +420,24 @@ int gj_submit_batch(gj_ctx* ctx, const uint32_t* src, const uint32_t* dst, const
     }
     S->cv_work.notify_all();
     *req_id = r->id;
+    return GJ_OK;
+}
+
+int gj_cancel(gj_ctx* ctx, uint64_t req_id) {
+    if (!ctx || !ctx->server) return GJ_E_INVALID;
+    gj_server* S = ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(req_id);
+        if (it == S->reqs.end()) return GJ_E_NOTFOUND;
+        Request* r = it->second;
+        auto p = std::find(S->pending.begin(), S->pending.end(), r);
+        if (p == S->pending.end()) return GJ_E_PENDING;  // started or finished: it runs to its end
+        S->pending.erase(p);
+        r->t_start = S->now();
+        finish(S, r, GJ_E_CANCELLED);
+    }
+    S->cv_done.notify_all();
     return GJ_OK;
 }
 

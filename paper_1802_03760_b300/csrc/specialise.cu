@@ -194,7 +194,7 @@ void gj_tri_release(gj_tri& t) {
 static int edge_map(gj_ctx* ctx, const gj_graph* g, gj_tri& t) {
     uint32_t bits = 1;
     while ((1ull << bits) < 2 * g->m) bits++;
-    GJ_CUDA_TRY(ctx, cudaMalloc(&t.emap, sizeof(uint4) << bits));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &t.emap, sizeof(uint4) << bits));
     GJ_CUDA_TRY(ctx, cudaMemsetAsync(t.emap, 0xff, sizeof(uint4) << bits, ctx->stream));
     if (g->m) {
         k_edge_map<<<grid_for(ctx, g->m), 256, 0, ctx->stream>>>(g->fwd.key, g->fwd.nbr, g->m, t.emap, bits);
@@ -208,9 +208,9 @@ static int edge_map(gj_ctx* ctx, const gj_graph* g, gj_tri& t) {
 // Hash sets of t's long lists (after its lists are written).
 static int tri_tables(gj_ctx* ctx, uint64_t m, gj_tri& t) {
     cudaStream_t st = ctx->stream;
-    GJ_CUDA_TRY(ctx, cudaMalloc(&t.tab_off, sizeof(int64_t) * (m + 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &t.tab_off, sizeof(int64_t) * (m + 1)));
     int64_t* size = nullptr;
-    GJ_CUDA_TRY(ctx, cudaMallocAsync(&size, sizeof(int64_t) * (m ? m : 1), st));
+    GJ_CUDA_TRY(ctx, gj_malloc_async(ctx, &size, sizeof(int64_t) * (m ? m : 1), st));
     if (m) {
         k_tri_tab_sizes<<<grid_for(ctx, m), 256, 0, st>>>(t.off, m, size);
         GJ_LAUNCHED(ctx);
@@ -222,7 +222,7 @@ static int tri_tables(gj_ctx* ctx, uint64_t m, gj_tri& t) {
         rc = GJ_E_CUDA;
     cudaFreeAsync(size, st);
     GJ_TRY(rc);
-    GJ_CUDA_TRY(ctx, cudaMalloc(&t.tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &t.tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
     if (tsz > 0) {
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(t.tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
         k_tri_tab_insert<<<(unsigned)ctx->sm_count * 8, 256, 0, st>>>(t.off, t.nbr, m, t.tab_off, t.tab);
@@ -237,10 +237,10 @@ int gj_tri_build(gj_ctx* ctx, gj_graph* g) {
     cudaStream_t st = ctx->stream;
     const uint64_t m = g->m;
     gj_tri t;
-    GJ_CUDA_TRY(ctx, cudaMalloc(&t.off, sizeof(int64_t) * (m + 1)));
+    GJ_CUDA_TRY(ctx, gj_malloc(ctx, &t.off, sizeof(int64_t) * (m + 1)));
     uint32_t* cnt = nullptr;
     unsigned long long* next = nullptr;
-    cudaError_t e = cudaMallocAsync(&cnt, sizeof(uint32_t) * (m ? m : 1) + 256, st);
+    cudaError_t e = gj_malloc_async(ctx, &cnt, sizeof(uint32_t) * (m ? m : 1) + 256, st);
     if (e != cudaSuccess) {
         gj_tri_release(t);
         gj_set_error(ctx, GJ_E_NOMEM, std::string("triangle index: ") + cudaGetErrorString(e));
@@ -265,7 +265,7 @@ int gj_tri_build(gj_ctx* ctx, gj_graph* g) {
     if (rc == GJ_OK) rc = gj_scan_u32(ctx, cnt, t.off, m);
     if (rc == GJ_OK && cudaMemcpyAsync(&total, t.off + m, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = GJ_E_CUDA;
     if (rc == GJ_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = GJ_E_CUDA;
-    if (rc == GJ_OK && cudaMalloc(&t.nbr, sizeof(uint32_t) * (size_t)(total ? total : 1)) != cudaSuccess) {
+    if (rc == GJ_OK && gj_malloc(ctx, &t.nbr, sizeof(uint32_t) * (size_t)(total ? total : 1)) != cudaSuccess) {
         cudaGetLastError();
         gj_set_error(ctx, GJ_E_NOMEM, "triangle index: out of device memory");
         rc = GJ_E_NOMEM;
@@ -292,9 +292,9 @@ int gj_graph_transform(gj_ctx* ctx, gj_graph* g, uint32_t flags) {
     const uint64_t m = g->m;
     uint32_t* map = nullptr;
     if (rename) {
-        GJ_CUDA_TRY(ctx, cudaMalloc(&map, sizeof(uint32_t) * n));
+        GJ_CUDA_TRY(ctx, gj_malloc(ctx, &map, sizeof(uint32_t) * n));
         uint64_t *keys = nullptr, *res = nullptr;
-        cudaError_t e = cudaMallocAsync(&keys, 16 * (size_t)n, st);
+        cudaError_t e = gj_malloc_async(ctx, &keys, 16 * (size_t)n, st);
         if (e != cudaSuccess) {
             cudaFree(map);
             gj_set_error(ctx, GJ_E_NOMEM, "degree renaming: out of device memory");
@@ -314,7 +314,7 @@ int gj_graph_transform(gj_ctx* ctx, gj_graph* g, uint32_t flags) {
         }
     }
     uint32_t* pairs = nullptr;
-    cudaError_t e = cudaMallocAsync(&pairs, 8 * (size_t)(m ? m : 1), st);
+    cudaError_t e = gj_malloc_async(ctx, &pairs, 8 * (size_t)(m ? m : 1), st);
     if (e != cudaSuccess) {
         if (map) cudaFree(map);
         gj_set_error(ctx, GJ_E_NOMEM, "degree renaming: out of device memory");

@@ -57,7 +57,8 @@ class WorkStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("seed_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32),
                 ("prefix_buffer_bytes", ctypes.c_uint64), ("fused_ms", ctypes.c_double), ("plain_ms", ctypes.c_double),
-                ("donation", ctypes.c_uint32), ("wait_ms", ctypes.c_uint32), ("fault", ctypes.c_uint32)]
+                ("donation", ctypes.c_uint32), ("wait_ms", ctypes.c_uint32), ("fault", ctypes.c_uint32),
+                ("fault_count", ctypes.c_uint32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -128,6 +129,7 @@ _SIGS = {
     "gj_ctx_stream": (_VP, [_VP]),
     "gj_launch_count": (ctypes.c_uint64, [_VP]),
     "gj_checked_build": (ctypes.c_int, []),
+    "gj_cancel": (ctypes.c_int, [_VP, ctypes.c_uint64]),
     "gj_sync": (ctypes.c_int, [_VP]),
 }
 
@@ -377,8 +379,8 @@ def checked_build() -> bool:
 
 
 def set_tuning(ctx: Context, seed_chunk: int = 32, blocks_per_sm: int = 0, prefix_buffer_bytes: int = 0,
-               donation: int = 0, wait_ms: int = 0, fault: int = 0):
-    t = Tuning(seed_chunk, blocks_per_sm, prefix_buffer_bytes, 0.0, 0.0, donation, wait_ms, fault)
+               donation: int = 0, wait_ms: int = 0, fault: int = 0, fault_count: int = 0):
+    t = Tuning(seed_chunk, blocks_per_sm, prefix_buffer_bytes, 0.0, 0.0, donation, wait_ms, fault, fault_count)
     _check(lib().gj_set_tuning(ctx._h, ctypes.byref(t)), ctx)
 
 
@@ -454,6 +456,15 @@ class Server:
                self.ctx)
         self._keep[rid.value] = list(qs)
         return rid.value
+
+    def cancel(self, rid: int) -> bool:
+        """gj_cancel: True if the request was withdrawn before it started,
+        False if it had already started (it runs to its end)."""
+        rc = lib().gj_cancel(self.ctx._h, rid)
+        if rc == -9:  # GJ_E_PENDING
+            return False
+        _check(rc, self.ctx)
+        return True
 
     def poll(self, rid: int, wait_ms: int = -1):
         """The request's result as a dict, or None while it is pending."""

@@ -6,7 +6,9 @@ submission order, through the synchronous API; and a request must give the
 same result alone as in the mix. Each wave balances its warps through a
 donation queue of its own; forcing every batch through it changes no
 result, and a wave whose bounded wait gives up fails its requests with
-GJ_E_TIMEOUT without stopping the loop."""
+GJ_E_TIMEOUT without stopping the loop. A request withdrawn before it
+starts (gj_cancel) is never run: the others give the results of the
+sequential replay without it."""
 import numpy as np
 import pytest
 
@@ -109,6 +111,41 @@ def test_wave_wait_gives_up_as_a_request_error():
     assert r["status"] == 0 and (r["counts"][0], r["checksums"][0]) == want
     srv.stop()
     ctx.close()
+
+
+def test_cancelled_requests_are_never_run():
+    scale = 13
+    n = 1 << scale
+    s, d = rmat_edges(scale, seed=61)
+    stream = UpdateStream(s, d, scale, seed=61)
+    reqs = []
+    for i in range(40):
+        if i % 2:
+            reqs.append(("count", None, ["triangle", "4-clique"]))
+        else:
+            reqs.append(("batch", stream.next_batch(2000), ["triangle"]))
+    ctx = gj.Context(0)
+    g = gj.Graph(ctx, s, d, n)
+    qmap = {nm: gj.Query(ctx, *QUERIES[nm]) for nm in QUERIES}
+    srv = gj.Server(g)
+    ids = [srv.submit_count([qmap[nm] for nm in names]) if kind == "count"
+           else srv.submit_batch(*batch, [qmap[nm] for nm in names]) for kind, batch, names in reqs]
+    # the newest first, while the loop works through the oldest
+    cancelled = [False] * 10 + [srv.cancel(i) for i in reversed(ids[10:])][::-1]
+    res = [srv.poll(i) for i in ids]
+    with pytest.raises(gj.GJError) as ei:
+        srv.cancel(ids[0])
+    assert ei.value.code == -10  # retired by the poll
+    srv.stop()
+    ctx.close()
+    assert any(cancelled)
+    for r, c in zip(res, cancelled):
+        assert (r["status"] == -12) == c  # GJ_E_CANCELLED
+    want = replay(s, d, n, [q for q, c in zip(reqs, cancelled) if not c])
+    got = [r for r, c in zip(res, cancelled) if not c]
+    for i, (r, (c, h, ver)) in enumerate(zip(got, want)):
+        assert r["status"] == 0, (i, r)
+        assert (r["counts"], r["checksums"], r["version"]) == (c, h, ver), i
 
 
 def test_request_alone_equals_in_mix():
