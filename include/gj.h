@@ -32,11 +32,15 @@
  *     thread at a time.
  *
  * Match checksum (not from the paper; fixed by this library so that listed
- * matches can be compared without sorting): H(x) = m(...m(m(m(k) ^ x_0) ^
- * x_1)... ^ x_{k-1}), the tuple in query attribute order, with m the
- * SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014); the checksum
- * of a set of matches is the sum of H over it modulo 2^64. Delta checksums
- * add H for gained matches and subtract it for lost ones.
+ * matches can be compared without sorting): H(x) = q(k) * f_0(x_0) * ... *
+ * f_{k-1}(x_{k-1}) modulo 2^64, x_a the value of query attribute a, with
+ * f_a(v) = m(v ^ s_a) | 1, q(k) = m(k) | 1, s_a = (a + 1) *
+ * 0x9e3779b97f4a7c15 and m the SplitMix64 output function (Steele, Lea,
+ * Flood, OOPSLA 2014); the checksum of a set of matches is the sum of H over
+ * it modulo 2^64. All factors are odd (units modulo 2^64), and the sum over
+ * matches that share some attributes factorises, so factorised output
+ * (Section 5.4) is checked without listing its matches. Delta checksums add
+ * H for gained matches and subtract it for lost ones.
  */
 #ifndef GJ_H
 #define GJ_H

@@ -24,9 +24,13 @@
  *     that do not constrain one another.
  *
  * The match checksum is not from the paper; it is the order-independent sum
- * (mod 2^64) over matches of H(x_1..x_k), H built from the SplitMix64 output
- * function (Steele, Lea, Flood, OOPSLA 2014), with the tuple in query
- * attribute order.
+ * (mod 2^64) over matches of H(x_0..x_{k-1}) = q(k) * f_0(x_0) * ... *
+ * f_{k-1}(x_{k-1}) (mod 2^64), with f_a(v) = m(v ^ s_a) | 1, q(k) = m(k) | 1,
+ * s_a = (a + 1) * 0x9e3779b97f4a7c15 and m the SplitMix64 output function
+ * (Steele, Lea, Flood, OOPSLA 2014); x_a is the value of query attribute a.
+ * Every factor is odd, so H is a product in the group of odd residues and
+ * the sum over a set of matches that agree on some attributes factorises
+ * (the factorised output of Section 5.4 sums it without listing the set).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -249,10 +253,15 @@ static uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-/* H of a match, tuple in query attribute order a_0..a_{k-1}. */
+/* H of a match, tuple in query attribute order a_0..a_{k-1}: the query's
+ * odd factor times one odd factor per attribute value, each salted by its
+ * attribute so that the same value at two attributes weighs differently. */
 static uint64_t tuple_hash(uint32_t k, const uint32_t* x_by_attr) {
-    uint64_t h = mix64(k);
-    for (uint32_t a = 0; a < k; a++) h = mix64(h ^ (uint64_t)x_by_attr[a]);
+    uint64_t h = mix64(k) | 1u;
+    for (uint32_t a = 0; a < k; a++) {
+        const uint64_t salt = (uint64_t)(a + 1) * 0x9e3779b97f4a7c15ULL;
+        h *= mix64((uint64_t)x_by_attr[a] ^ salt) | 1u;
+    }
     return h;
 }
 

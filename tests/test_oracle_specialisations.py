@@ -28,9 +28,10 @@ def py_mix64(z):
 
 
 def py_hash(t):
-    h = py_mix64(len(t))
-    for x in t:
-        h = py_mix64(h ^ int(x))
+    """H(t) = q(k) * prod_a f_a(t_a) mod 2^64 (odd factors; see include/gj.h)."""
+    h = py_mix64(len(t)) | 1
+    for a, x in enumerate(t):
+        h = (h * (py_mix64(int(x) ^ (((a + 1) * 0x9E3779B97F4A7C15) & M64)) | 1)) & M64
     return h
 
 
