@@ -94,52 +94,47 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 }
 
 // Shared-memory layout of one warp (identical on host and device): the
-// plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), the
-// buffer of matches waiting to be hashed for an aggregated group, then per
-// level j >= 2 the prefix tuples [j][FC] (column-major), the min-list
-// pointers [FC], the candidate offsets [FC + 1], the hash prefixes [FC], the
-// min-i bytes [FC] and the group sizes [FC]. Offsets are closed forms so
-// that no per-level table sits in local memory.
+// plan, 4 x 8 scalars (n, cursor, total, cursor's prefix per level), then
+// per level j >= 2 the prefix tuples [j][FC] (column-major), the min-list
+// pointers [FC], the candidate offsets [FC + 1] and the min-i bytes [FC]
+// (delta plans add the new-version parts of each min list and the seed's
+// sign), then one block that only the query's last level uses: the hash
+// factor of each prefix [FC] and, in EXT launches, the other binding list
+// of a two-binding last level [FC] (pointer, hash set, length) and the size
+// of each aggregated group [FC]. A warp finishes a last-level batch before
+// it activates another one, so one block serves every query. Offsets are
+// closed forms so that no per-level table sits in local memory.
 constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
-// Matches of an aggregated last-level group wait here until 32 or more can
-// be hashed against every member of the group at once (EXT launches only).
-constexpr uint32_t SV_CAP = 96;
-constexpr uint32_t SV_BYTES = SV_CAP * 4;
-static_assert(31 + 2 * 32 <= SV_CAP, "a step adds up to 64 matches to fewer than 32 buffered ones");
-constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + FC * 8 + FC;  // mptr + cs + hpre + minb
-// EXT launches also keep the size of each aggregated group (at its leader).
-constexpr uint32_t GRP_BYTES = FC;
+constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + ALIGN16(FC);  // mptr + cs + minb
 // Delta plans also keep, per prefix, the new-version parts of the min list
 // (inserts, deletes, committed length) and the seed's sign.
 constexpr uint32_t LVL_DELTA = FC * 8 + FC * 8 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
-__host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d, bool x) {
-    return LVL_FIXED + (x ? GRP_BYTES : 0) + (d ? ALIGN16(LVL_DELTA) : 0);
-}
-__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d, bool x) {
+__host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d) { return LVL_FIXED + (d ? ALIGN16(LVL_DELTA) : 0); }
+__host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d) {
     // sum over i = 2..j-1 of (FC * i * 4 + fixed part)
-    return PLAN_BYTES + SCAL_BYTES + (x ? SV_BYTES : 0) + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) +
-           lvl_size_fixed(d, x) * (j - 2);
+    return PLAN_BYTES + SCAL_BYTES + (uint32_t)(FC * 4) * ((j * (j - 1)) / 2 - 1) + lvl_size_fixed(d) * (j - 2);
 }
-__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d, bool x) { return lvl_base(j, d, x); }
-__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d, bool x) {
-    return lvl_base(j, d, x) + FC * 4 * j;
-}
+__host__ __device__ __forceinline__ uint32_t off_tup(uint32_t j, bool d, bool) { return lvl_base(j, d); }
+__host__ __device__ __forceinline__ uint32_t off_mptr(uint32_t j, bool d, bool) { return lvl_base(j, d) + FC * 4 * j; }
 __host__ __device__ __forceinline__ uint32_t off_cs(uint32_t j, bool d, bool x) { return off_mptr(j, d, x) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t j, bool d, bool x) {
+__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d, bool x) {
     return off_cs(j, d, x) + ALIGN16((FC + 1) * 8);
 }
-__host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d, bool x) { return off_hpre(j, d, x) + FC * 8; }
-// group size of an aggregated last-level prefix (leaders only)
-__host__ __device__ __forceinline__ uint32_t off_grp(uint32_t j, bool d, bool x) { return off_minb(j, d, x) + FC; }
-__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j, bool x) { return off_minb(j, true, x) + FC + (x ? GRP_BYTES : 0); }
+__host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j, bool x) { return off_minb(j, true, x) + ALIGN16(FC); }
 __host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j, bool x) { return off_dins(j, x) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j, bool x) { return off_ddel(j, x) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j, bool x) { return off_dblen(j, x) + FC * 4; }
 __host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j, bool x) { return off_dndel(j, x) + FC * 4; }
+// the last-level block, after the levels of the launch's longest query
+__host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t kmax, bool d, bool) { return lvl_base(kmax, d); }
+__host__ __device__ __forceinline__ uint32_t off_olp(uint32_t kmax, bool d, bool x) { return off_hpre(kmax, d, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_olt(uint32_t kmax, bool d, bool x) { return off_olp(kmax, d, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_oll(uint32_t kmax, bool d, bool x) { return off_olt(kmax, d, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_grp(uint32_t kmax, bool d, bool x) { return off_oll(kmax, d, x) + FC * 4; }
 __host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d, bool x) {
-    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES + (x ? SV_BYTES : 0) : lvl_base(kmax, d, x);
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : off_hpre(kmax, d, x) + FC * 8 + (x ? ALIGN16(FC * 8 + FC * 8 + FC * 4 + FC) : 0);
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
@@ -237,7 +232,6 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     uint64_t* cur_ = n_ + GJ_MAX_K;
     uint64_t* tot_ = cur_ + GJ_MAX_K;
     uint64_t* ip_ = tot_ + GJ_MAX_K;  // prefix that owns candidate cur_ (advances monotonically)
-    uint32_t* sv = reinterpret_cast<uint32_t*>(ws + PLAN_BYTES + SCAL_BYTES);  // [SV_CAP]
     const GraphView& G = A.G;
     const uint64_t space = A.qbase[A.nq];
 
@@ -268,17 +262,17 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
     };
 
     // Count step for level j: min-c / min-i per prefix, scan of min-c. At
-    // the last level also the hash of each prefix's attributes that precede
-    // the new one in query order (the tuple hash is a left fold).
+    // the last level also each prefix's factor of the match hash (the
+    // query's factor times those of its k - 1 values), and in EXT launches
+    // the other list of a two-binding level, kept for the extension step.
     auto activate = [&](int j, bool count_stats = true) {
         const uint32_t nj = (uint32_t)n_[j];
         uint32_t* tup = reinterpret_cast<uint32_t*>(ws + off_tup(j, DELTA, EXT));
         const uint32_t** mptr = reinterpret_cast<const uint32_t**>(ws + off_mptr(j, DELTA, EXT));
         uint64_t* cs = reinterpret_cast<uint64_t*>(ws + off_cs(j, DELTA, EXT));
-        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(j, DELTA, EXT));
+        uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(A.kmax, DELTA, EXT));
         uint8_t* minb = ws + off_minb(j, DELTA, EXT);
         const bool last = (j == (int)k - 1);
-        const uint32_t a_new = P.order[j];
         // aggregation: a prefix that agrees with the one before it on every
         // position the last level reads has the same extensions; it joins
         // that prefix's group and proposes nothing itself
@@ -322,15 +316,26 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     reinterpret_cast<uint32_t*>(ws + off_dblen(j, EXT))[i] = bl.base_len;
                     reinterpret_cast<uint32_t*>(ws + off_dndel(j, EXT))[i] = bl.ndel;
                 } else {
+                    // EXT, last level with two bindings: keep the other list
+                    const bool keep_other = EXT && last && P.nb[j] == 2;
+                    BindList other{G.fn, 0u, nullptr, 0u}, bestL{G.fn, 0u, nullptr, 0u};
                     for (uint32_t b = 0; b < P.nb[j]; b++) {
                         uint32_t v = tup[P.bpos[j][b] * FC + i];
                         const uint32_t dir = P.bdir[j][b];
                         uint64_t len;
                         const uint32_t* lp;
-                        if (EXT && dir == GJ_BIND_TRI) {
+                        if (EXT && (dir == GJ_BIND_TRI || keep_other)) {
                             const BindList L = gj_bind_list(G, dir, v, tup[P.bpos2[j][b] * FC + i]);
                             len = L.len;
                             lp = L.p;
+                            if (keep_other) {
+                                if (len < best) {
+                                    other = bestL;
+                                    bestL = L;
+                                } else {
+                                    other = L;
+                                }
+                            }
                         } else if (GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) {
                             const int64_t* off = dir ? G.ro : G.fo;
                             int64_t s = __ldg(off + v);
@@ -347,14 +352,19 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             bp = lp;
                         }
                     }
+                    if (keep_other) {
+                        reinterpret_cast<const uint32_t**>(ws + off_olp(A.kmax, DELTA, EXT))[i] = other.p;
+                        reinterpret_cast<const uint32_t**>(ws + off_olt(A.kmax, DELTA, EXT))[i] = other.bits ? other.tab : nullptr;
+                        reinterpret_cast<uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[i] = other.len;
+                    }
                     all2 += best;
                     if (!lead) best = 0;
                 }
                 mptr[i] = bp;
                 minb[i] = (uint8_t)bi;
                 if (last) {
-                    uint64_t hh = gj_mix64((uint64_t)k);
-                    for (uint32_t a = 0; a < a_new; a++) hh = gj_mix64(hh ^ (uint64_t)tup[P.qpos[a] * FC + i]);
+                    uint64_t hh = gj_hq(k);
+                    for (uint32_t p = 0; p < (uint32_t)j; p++) hh *= gj_hf(P.order[p], tup[p * FC + i]);
                     hpre[i] = hh;
                 }
             }
@@ -365,7 +375,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         if (aggm) {
             const uint32_t l0 = __ballot_sync(0xffffffffu, lead2[0]), l1 = __ballot_sync(0xffffffffu, lead2[1]);
             const uint64_t L = (uint64_t)l0 | ((uint64_t)l1 << 32);
-            uint8_t* grp = ws + off_grp(j, DELTA, EXT);
+            uint8_t* grp = ws + off_grp(A.kmax, DELTA, EXT);
+            uint32_t gend[2] = {0, 0};
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const uint32_t i = lane + 32 * h;
@@ -373,6 +384,20 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     const uint64_t rest = i + 1 < 64 ? (L >> (i + 1)) : 0ull;
                     const uint32_t next = rest ? i + 1 + (uint32_t)__ffsll((long long)rest) - 1 : nj;
                     grp[i] = (uint8_t)(next - i);
+                    gend[h] = next;
+                }
+            }
+            __syncwarp();
+            // a group's matches are its members' prefixes times the leader's
+            // extensions: the sum of their hashes is (sum of the members'
+            // factors) x (the extension's factor), so the leader keeps the sum
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t i = lane + 32 * h;
+                if (lead2[h]) {
+                    uint64_t sum = hpre[i];
+                    for (uint32_t m = i + 1; m < gend[h]; m++) sum += hpre[m];
+                    hpre[i] = sum;
                 }
             }
         }
@@ -594,11 +619,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             }
             if (k == 2) {
                 if (keep) {
-                    uint64_t h = gj_mix64(2ull);
-                    uint32_t v0 = P.qpos[0] == 0 ? x0 : x1;
-                    uint32_t v1 = P.qpos[1] == 0 ? x0 : x1;
-                    h = gj_mix64(h ^ (uint64_t)v0);
-                    h = gj_mix64(h ^ (uint64_t)v1);
+                    const uint64_t h = gj_hq(2) * gj_hf(P.order[0], x0) * gj_hf(P.order[1], x1);
                     chk += sg > 0 ? h : 0ull - h;
                 }
                 cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
@@ -638,13 +659,13 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA, EXT));
             const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA, EXT));
             const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j, DELTA, EXT));
-            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(j, DELTA, EXT));
+            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(A.kmax, DELTA, EXT));
             const uint8_t* minb = ws + off_minb(j, DELTA, EXT);
             const bool last = (j == (int)k - 1);
             const uint32_t nb = P.nb[j];
             const uint32_t a_new = P.order[j];
             uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA, EXT));
-            const uint8_t* grp = ws + off_grp(j, DELTA, EXT);
+            const uint8_t* grp = ws + off_grp(A.kmax, DELTA, EXT);
             const bool agg = EXT && !DELTA && last && P.agg;
             // other binding lists cached in registers for a step-uniform prefix:
             // two for plain edge queries (up to 4-cliques), one in the extended
@@ -657,20 +678,28 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             uint64_t hi_ex = 1ull << 32;
             // the other binding lists and the inequality bounds of prefix pi, in registers
             auto cache_prefix = [&](uint32_t pi) {
-                const uint32_t b0 = minb[pi];
-                uint32_t o = 0;
-                for (uint32_t b = 0; b < nb; b++) {
-                    if (b == b0) continue;
-                    const uint32_t dir = EXT ? P.bdir[j][b] : (P.bdir[j][b] & 1u);
-                    const BindList L = gj_bind_list(G, dir, tup[P.bpos[j][b] * FC + pi], tup[P.bpos2[j][b] * FC + pi]);
+                if (EXT && last && nb == 2) {  // the other list, kept by the count step
+                    const uint32_t* t = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT))[pi];
+                    ol[0] = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[pi];
+                    ob[0] = t ? t : reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[pi];
+                    obits[0] = t ? gj_tab_bits(ol[0]) : 0u;
+                } else {
+                    const uint32_t b0 = minb[pi];
+                    uint32_t o = 0;
+                    for (uint32_t b = 0; b < nb; b++) {
+                        if (b == b0) continue;
+                        const uint32_t dir = EXT ? P.bdir[j][b] : (P.bdir[j][b] & 1u);
+                        const BindList L =
+                            gj_bind_list(G, dir, tup[P.bpos[j][b] * FC + pi], tup[P.bpos2[j][b] * FC + pi]);
 #pragma unroll
-                    for (int q = 0; q < MAXO; q++)
-                        if (q == (int)o) {
-                            ob[q] = L.bits ? L.tab : L.p;
-                            ol[q] = L.len;
-                            obits[q] = L.bits;
-                        }
-                    o++;
+                        for (int q = 0; q < MAXO; q++)
+                            if (q == (int)o) {
+                                ob[q] = L.bits ? L.tab : L.p;
+                                ol[q] = L.len;
+                                obits[q] = L.bits;
+                            }
+                        o++;
+                    }
                 }
                 lo_in = 0;
                 hi_ex = 1ull << 32;
@@ -680,30 +709,6 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     else lo_in = v + 1 > lo_in ? v + 1 : lo_in;
                 }
                 cached = pi;
-            };
-            // hashes the nsv buffered matches against every member of the group
-            // that starts at prefix g0 (g members): count += nsv * g. The g * nsv
-            // (member, match) pairs are dealt to the lanes in turn, so every lane
-            // hashes the same number of them.
-            auto flush_group = [&](uint32_t g0, uint32_t g, uint32_t nsv) {
-                cnt += (unsigned long long)nsv * g;
-                uint32_t mbr = g0, t = lane;  // pair lane + 32 i is (member, match) = (mbr, t)
-                while (t >= nsv) {
-                    t -= nsv;
-                    mbr++;
-                }
-                const uint32_t gend = g0 + g;
-                while (mbr < gend) {
-                    uint64_t h = gj_mix64(hpre[mbr] ^ (uint64_t)sv[t]);
-                    for (uint32_t a = a_new + 1; a < k; a++) h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
-                    chk += h;
-                    t += 32;  // once nsv >= 32 (every flush but a group's last) at most one wrap
-                    while (t >= nsv) {
-                        t -= nsv;
-                        mbr++;
-                    }
-                }
-                __syncwarp();
             };
             uint64_t cur = cur_[j];
             uint32_t ip = (uint32_t)ip_[j];
@@ -752,8 +757,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     // Last level, next 64 candidates all in prefix ip: two per
                     // lane, with their probes interleaved.
                     if (ip != cached) cache_prefix(ip);
-                    const uint32_t gsz = (EXT && agg) ? grp[ip] : 1u;  // prefixes whose matches these candidates make
-                    uint32_t nsv = 0;
+                    // prefixes whose matches these candidates make (hp is then
+                    // the sum of their hash factors)
+                    const uint32_t gsz = (EXT && agg) ? grp[ip] : 1u;
                     // Up to 16 steps on prefix ip alone, its invariants in
                     // registers and 32-bit offsets r into its min list. When
                     // the warp's range [cur, tot) ends inside prefix ip (its
@@ -783,33 +789,12 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                                 else member32x2(ob[q], ol[q], e0, k0, e1, k1);
                             }
                         }
-                        if (!EXT || gsz == 1) {
-                            if (k0 | k1) {
-                                uint64_t h0 = gj_mix64(hp ^ (uint64_t)e0), h1 = gj_mix64(hp ^ (uint64_t)e1);
-                                for (uint32_t a = a_new + 1; a < k; a++) {
-                                    const uint64_t x = (uint64_t)tup[P.qpos[a] * FC + ip];
-                                    h0 = gj_mix64(h0 ^ x);
-                                    h1 = gj_mix64(h1 ^ x);
-                                }
-                                chk += (k0 ? h0 : 0ull) + (k1 ? h1 : 0ull);
-                            }
-                            cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
-                        } else {
-                            // an aggregated group: buffer the step's matches, hash
-                            // them against every member once 32 are waiting
-                            const uint32_t m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
-                            if (k0) sv[nsv + __popc(m0 & lt)] = e0;
-                            if (k1) sv[nsv + __popc(m0) + __popc(m1 & lt)] = e1;
-                            nsv += __popc(m0) + __popc(m1);
-                            __syncwarp();
-                            if (nsv >= 32) {  // at most 31 + 64 < SV_CAP are ever buffered
-                                flush_group(ip, gsz, nsv);
-                                nsv = 0;
-                            }
-                        }
+                        if (k0) chk += hp * gj_hf(a_new, e0);
+                        if (k1) chk += hp * gj_hf(a_new, e1);
+                        const uint32_t c2 = __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                        cnt += EXT ? (unsigned long long)c2 * gsz : (unsigned long long)c2;
                         r += 64;
                     } while (++steps < 16 && r < rend && (tail_ok || rend - r >= 64));
-                    if (EXT && nsv) flush_group(ip, gsz, nsv);
                     cur = c0 + r;
                     continue;
                 }
@@ -860,6 +845,15 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     for (int q = 0; q < MAXO; q++)
                         if (q + 1 < (int)nb && keep)
                             keep = obits[q] ? gj_tab_member(ob[q], obits[q], e) : member32(ob[q], ol[q], e);
+                } else if (EXT && last && nb == 2) {
+                    // the other list, kept by the count step
+                    if (keep) {
+                        const uint32_t* t = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT))[i];
+                        const uint32_t len = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[i];
+                        keep = t ? gj_tab_member(t, gj_tab_bits(len), e)
+                                 : gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[i],
+                                               len, e);
+                    }
                 } else if (EXT) {
                     // The lanes of one prefix look its lists up once: the first
                     // lane of each run of equal prefixes resolves them and the
@@ -892,14 +886,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
                 cur += 32;
                 if (last) {
-                    const uint32_t gsz = (EXT && agg && keep) ? grp[i] : 1u;  // members of an aggregated group
+                    // members of an aggregated group (hpre[i] sums their factors)
+                    const uint32_t gsz = (EXT && agg && keep) ? grp[i] : 1u;
                     if (keep) {
-                        for (uint32_t mbr = i; mbr < i + gsz; mbr++) {
-                            uint64_t h = gj_mix64(hpre[mbr] ^ (uint64_t)e);
-                            for (uint32_t a = a_new + 1; a < k; a++)
-                                h = gj_mix64(h ^ (uint64_t)tup[P.qpos[a] * FC + mbr]);
-                            chk += (!DELTA || sg > 0) ? h : 0ull - h;
-                        }
+                        const uint64_t h = hpre[i] * gj_hf(a_new, e);
+                        chk += (!DELTA || sg > 0) ? h : 0ull - h;
                     }
                     if (DELTA)
                         cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -

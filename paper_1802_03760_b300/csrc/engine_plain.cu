@@ -35,9 +35,11 @@ struct Acc {
     unsigned long long* tup;    // slot cursor of listed matches
 };
 
+// H of the match whose value at position p is xs[p] (position p binds query
+// attribute P.order[p]).
 __device__ __forceinline__ uint64_t hash_positions(const Plan& P, const uint32_t* xs) {
-    uint64_t h = gj_mix64((uint64_t)P.k);
-    for (uint32_t a = 0; a < P.k; a++) h = gj_mix64(h ^ (uint64_t)xs[P.qpos[a]]);
+    uint64_t h = gj_hq(P.k);
+    for (uint32_t p = 0; p < P.k; p++) h *= gj_hf(P.order[p], xs[p]);
     return h;
 }
 

@@ -441,10 +441,18 @@ int gj_fused_enqueue(gj_ctx* ctx, const GraphView& G, const Plan* hp, uint32_t n
 
 // ------------------------------------------------------------------ device helpers
 
-__device__ __forceinline__ uint64_t gj_mix64(uint64_t z) {
+__host__ __device__ __forceinline__ uint64_t gj_mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
     return z ^ (z >> 31);
+}
+
+// Factors of the match hash H(x) = q(k) * prod_a f_a(x_a) mod 2^64 (the
+// checksum's summand, defined in gj.h): the query's factor and attribute
+// a's factor of the value v, all odd.
+__host__ __device__ __forceinline__ uint64_t gj_hq(uint32_t k) { return gj_mix64((uint64_t)k) | 1ull; }
+__host__ __device__ __forceinline__ uint64_t gj_hf(uint32_t a, uint32_t v) {
+    return gj_mix64((uint64_t)v ^ ((uint64_t)(a + 1) * 0x9e3779b97f4a7c15ULL)) | 1ull;
 }
 
 // Membership of e in the sorted list a[0..len): branch-free binary search
