@@ -34,6 +34,7 @@ struct Bundle {
     uint32_t plan, level, n, pad;
     unsigned long long c_lo, c_hi;  // candidate range of the batch to extend (all: 0, ~0)
     uint32_t tup[GJ_MAX_K][FC];
+    uint64_t hp[FC];  // a factorised last level's hash factors (the count weights are in tup)
     int8_t sg[FC];
 };
 
@@ -277,6 +278,19 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         // position the last level reads has the same extensions; it joins
         // that prefix's group and proposes nothing itself
         const uint32_t aggm = (EXT && !DELTA && last) ? P.agg : 0u;
+        // factorised output: at level k-2 the per-parent counters start at
+        // zero; at the last level row i stands for w_i prefixes (its weight,
+        // in the unread column k-2) and hpre already holds its factor sum
+        const bool factl = EXT && !DELTA && last && P.fact;
+        if (EXT && !DELTA && P.fact && j == (int)k - 2) {
+            uint32_t* acc_n = reinterpret_cast<uint32_t*>(ws + off_tup(j + 1, DELTA, EXT)) + j * FC;
+            acc_n[lane] = 0;
+            acc_n[lane + 32] = 0;
+            hpre[lane] = 0;
+            hpre[lane + 32] = 0;
+            __syncwarp();
+        }
+        uint64_t wsum = 0;  // factorised last level: the prefixes the rows stand for
         uint64_t len2[2];
         uint64_t all2 = 0;  // the min counts of every prefix, members of groups included
         bool lead2[2];
@@ -362,7 +376,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
                 mptr[i] = bp;
                 minb[i] = (uint8_t)bi;
-                if (last) {
+                if (factl) {
+                    const uint32_t w = tup[(j - 1) * FC + i];
+                    wsum += w;
+                    all2 += (uint64_t)w * best - best;  // the row counted once above
+                } else if (last) {
                     uint64_t hh = gj_hq(k);
                     for (uint32_t p = 0; p < (uint32_t)j; p++) hh *= gj_hf(P.order[p], tup[p * FC + i]);
                     hpre[i] = hh;
@@ -370,8 +388,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             }
             len2[h] = best;
         }
-        if (aggm)
+        if (aggm || factl)
             for (int o = 16; o > 0; o >>= 1) all2 += __shfl_xor_sync(0xffffffffu, all2, o);
+        if (factl)
+            for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
         if (aggm) {
             const uint32_t l0 = __ballot_sync(0xffffffffu, lead2[0]), l1 = __ballot_sync(0xffffffffu, lead2[1]);
             const uint64_t L = (uint64_t)l0 | ((uint64_t)l1 << 32);
@@ -423,9 +443,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
         // work units of the cost model count every prefix, also those whose
         // extensions an aggregated group shares
         if (lane == 0 && count_stats) {
-            stat_add(A.stats, 0, j, nj);
-            stat_add(A.stats, 1, j, (unsigned long long)nj * P.nb[j]);
-            stat_add(A.stats, 2, j, aggm ? all2 : total);
+            const uint64_t rows = factl ? wsum : nj;
+            stat_add(A.stats, 0, j, rows);
+            stat_add(A.stats, 1, j, (unsigned long long)rows * P.nb[j]);
+            stat_add(A.stats, 2, j, (aggm || factl) ? all2 : total);
         }
     };
 
@@ -555,6 +576,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     for (uint32_t i = lane; i < nb_; i += 32) tupL[c * FC + i] = Bd.tup[c][i];
                 if (DELTA)
                     for (uint32_t i = lane; i < nb_; i += 32) reinterpret_cast<int8_t*>(ws + off_dsg(L, EXT))[i] = Bd.sg[i];
+                if (EXT && !DELTA && P.fact && L == k - 1)
+                    for (uint32_t i = lane; i < nb_; i += 32)
+                        reinterpret_cast<uint64_t*>(ws + off_hpre(A.kmax, DELTA, EXT))[i] = Bd.hp[i];
                 const unsigned long long c_lo = Bd.c_lo, c_hi = Bd.c_hi;
                 __syncwarp();
                 if (lane == 0) {
@@ -659,9 +683,15 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const uint32_t* tup = reinterpret_cast<const uint32_t*>(ws + off_tup(j, DELTA, EXT));
             const uint32_t* const* mptr = reinterpret_cast<const uint32_t* const*>(ws + off_mptr(j, DELTA, EXT));
             const uint64_t* cs = reinterpret_cast<const uint64_t*>(ws + off_cs(j, DELTA, EXT));
-            const uint64_t* hpre = reinterpret_cast<const uint64_t*>(ws + off_hpre(A.kmax, DELTA, EXT));
+            uint64_t* hpre = reinterpret_cast<uint64_t*>(ws + off_hpre(A.kmax, DELTA, EXT));
             const uint8_t* minb = ws + off_minb(j, DELTA, EXT);
             const bool last = (j == (int)k - 1);
+            // factorised output: level k-2 only counts and sums the factors of
+            // each parent's extensions (into the last level's weight column
+            // and hpre); the last level weighs each row by its weight
+            const bool factj = EXT && !DELTA && P.fact && j == (int)k - 2;
+            const bool factl = EXT && !DELTA && P.fact && last;
+            uint32_t* acc_n = reinterpret_cast<uint32_t*>(ws + off_tup(j + 1, DELTA, EXT)) + j * FC;
             const uint32_t nb = P.nb[j];
             const uint32_t a_new = P.order[j];
             uint32_t* nt = reinterpret_cast<uint32_t*>(ws + off_tup(last ? j : j + 1, DELTA, EXT));
@@ -739,6 +769,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         if (DELTA)
                             for (uint32_t i2 = lane; i2 < nj; i2 += 32)
                                 Bd.sg[i2] = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[i2];
+                        if (factl)
+                            for (uint32_t i2 = lane; i2 < nj; i2 += 32) Bd.hp[i2] = hpre[i2];
                         if (lane == 0) {
                             Bd.plan = (uint32_t)cur_q;
                             Bd.level = (uint32_t)j;
@@ -753,13 +785,14 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     }
                 }
                 while (ip + 1 < nj && cs[ip + 1] <= cur) ip++;
-                if (!DELTA && last && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
-                    // Last level, next 64 candidates all in prefix ip: two per
-                    // lane, with their probes interleaved.
+                if (!DELTA && (last || factj) && nb - 1 <= (uint32_t)MAXO && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
+                    // Last level (or a factorised level k-2), next 64
+                    // candidates all in prefix ip: two per lane, with their
+                    // probes interleaved.
                     if (ip != cached) cache_prefix(ip);
                     // prefixes whose matches these candidates make (hp is then
                     // the sum of their hash factors)
-                    const uint32_t gsz = (EXT && agg) ? grp[ip] : 1u;
+                    const uint32_t gsz = (EXT && agg) ? grp[ip] : (factl ? tup[(j - 1) * FC + ip] : 1u);
                     // Up to 16 steps on prefix ip alone, its invariants in
                     // registers and 32-bit offsets r into its min list. When
                     // the warp's range [cur, tot) ends inside prefix ip (its
@@ -773,6 +806,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     const uint64_t hp = hpre[ip];
                     uint32_t r = (uint32_t)(cur - c0);
                     uint32_t steps = 0;
+                    uint64_t sacc = 0;  // factorised level k-2: the step's factor sum and count
+                    uint32_t nacc = 0;
                     do {
                         const uint32_t q0 = r + lane, q1 = r + 32 + lane;
                         bool k0 = q0 < rend, k1 = q1 < rend;
@@ -789,12 +824,27 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                                 else member32x2(ob[q], ol[q], e0, k0, e1, k1);
                             }
                         }
-                        if (k0) chk += hp * gj_hf(a_new, e0);
-                        if (k1) chk += hp * gj_hf(a_new, e1);
                         const uint32_t c2 = __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
-                        cnt += EXT ? (unsigned long long)c2 * gsz : (unsigned long long)c2;
+                        if (EXT && factj) {
+                            if (k0) sacc += gj_hf(a_new, e0);
+                            if (k1) sacc += gj_hf(a_new, e1);
+                            nacc += c2;
+                        } else {
+                            if (k0) chk += hp * gj_hf(a_new, e0);
+                            if (k1) chk += hp * gj_hf(a_new, e1);
+                            cnt += EXT ? (unsigned long long)c2 * gsz : (unsigned long long)c2;
+                        }
                         r += 64;
                     } while (++steps < 16 && r < rend && (tail_ok || rend - r >= 64));
+                    if (EXT && factj) {
+                        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        if (lane == 0 && nacc) {
+                            acc_n[ip] += nacc;
+                            hpre[ip] += sacc;
+                            stat_add(A.stats, 3, j + 1, nacc);
+                        }
+                        __syncwarp();
+                    }
                     cur = c0 + r;
                     continue;
                 }
@@ -886,19 +936,36 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 }
                 cur += 32;
                 if (last) {
-                    // members of an aggregated group (hpre[i] sums their factors)
+                    // members of an aggregated group, or the prefixes a
+                    // factorised row stands for (hpre[i] sums their factors)
                     const uint32_t gsz = (EXT && agg && keep) ? grp[i] : 1u;
                     if (keep) {
                         const uint64_t h = hpre[i] * gj_hf(a_new, e);
                         chk += (!DELTA || sg > 0) ? h : 0ull - h;
                     }
-                    if (DELTA)
+                    if (DELTA) {
                         cnt += __popc(__ballot_sync(0xffffffffu, keep && sg > 0)) -
                                __popc(__ballot_sync(0xffffffffu, keep && sg < 0));
-                    else if (EXT && agg)
+                    } else if (EXT && factl) {
+                        unsigned long long w = keep ? tup[(j - 1) * FC + i] : 0u;
+                        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                        cnt += w;
+                    } else if (EXT && agg) {
                         cnt += __reduce_add_sync(0xffffffffu, keep ? gsz : 0u);
-                    else
+                    } else {
                         cnt += __popc(__ballot_sync(0xffffffffu, keep));
+                    }
+                    continue;
+                }
+                if (EXT && factj) {
+                    // count the extension and add its factor to its parent's sum
+                    if (keep) {
+                        atomicAdd(acc_n + i, 1u);
+                        atomicAdd(reinterpret_cast<unsigned long long*>(hpre + i),
+                                  (unsigned long long)gj_hf(a_new, e));
+                    }
+                    const uint32_t c1 = __popc(__ballot_sync(0xffffffffu, keep));
+                    if (lane == 0) stat_add(A.stats, 3, j + 1, c1);
                     continue;
                 }
                 const uint32_t mask = __ballot_sync(0xffffffffu, keep);
@@ -955,6 +1022,45 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 if (!last) n_[j + 1] = nn;
             }
             __syncwarp();
+            if (EXT && factj) {
+                // The level-(k-2) batch (or this warp's range of it) is done:
+                // every parent with extensions becomes one row of the last
+                // level's batch, with its weight (extension count) in the
+                // unread column k-2 and its factor sum (the parent's factors
+                // times the sum of its extensions' factors) in hpre.
+                uint32_t* tK = acc_n - j * FC;
+                uint32_t w[2];
+                uint64_t f[2];
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t i = lane + 32 * h;
+                    w[h] = i < nj ? acc_n[i] : 0u;
+                    f[h] = 0;
+                    if (w[h]) {
+                        uint64_t hh = gj_hq(k);
+                        for (uint32_t p = 0; p < (uint32_t)j; p++) hh *= gj_hf(P.order[p], tup[p * FC + i]);
+                        f[h] = hh * hpre[i];
+                    }
+                }
+                const uint32_t m0 = __ballot_sync(0xffffffffu, w[0] != 0), m1 = __ballot_sync(0xffffffffu, w[1] != 0);
+                __syncwarp();
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const uint32_t i = lane + 32 * h;
+                    if (w[h]) {
+                        const uint32_t d = h ? __popc(m0) + __popc(m1 & lt) : __popc(m0 & lt);
+                        for (uint32_t p = 0; p < (uint32_t)j; p++) tK[p * FC + d] = tup[p * FC + i];
+                        tK[j * FC + d] = w[h];
+                        hpre[d] = f[h];
+                    }
+                }
+                __syncwarp();
+                const uint32_t rows = __popc(m0) + __popc(m1);
+                if (lane == 0) n_[j + 1] = rows;
+                __syncwarp();
+                if (rows) act = j + 1;
+                continue;
+            }
             if (descend) act = j + 1;
             continue;
         }

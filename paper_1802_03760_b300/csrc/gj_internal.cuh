@@ -186,6 +186,13 @@ struct Plan {
     // positions have the same extensions, so consecutive ones are extended
     // once. 0: off (some list reads every earlier position, or delta plans).
     uint32_t agg;
+    // Factorised output (Section 5.4): 1 if the last level reads every
+    // position before k-2 and not position k-2 itself (k >= 4, static
+    // plans). Then the extensions of a level-(k-2) prefix are never
+    // materialised: the fused engine counts them (n) and sums their hash
+    // factors (S) per level-(k-3) parent, extends each parent once at the
+    // last level and weighs its matches by n (count) and S (checksum).
+    uint32_t fact;
     uint32_t delta;  // 1: seeds are the batch's signed changes of atom seed_atom
 };
 

@@ -46,7 +46,7 @@ uint32_t last_level_reads(const Plan* p) {
 }  // namespace
 
 bool gj_plan_ext(const Plan& p) {
-    if (p.agg) return true;
+    if (p.agg || p.fact) return true;
     for (uint32_t j = 1; j < p.k; j++) {
         if (p.nlt[j]) return true;
         for (uint32_t b = 0; j >= 2 && b < p.nb[j]; b++)
@@ -153,6 +153,12 @@ int gj_plan_compile(const gj_query* q, Plan* p, std::string* why) {
         const uint32_t all = (1u << (k - 1)) - 1, reads = last_level_reads(p), skip = all & ~reads;
         const bool suffix = skip && ((skip + (skip & (0u - skip))) & all) == 0;  // one run of bits ending at k-2
         p->agg = suffix ? reads : 0u;
+        // exactly position k-2 unread: its extensions factorise per parent
+        // (subsumes the aggregation of equal neighbours at the last level)
+        if (k >= 4 && skip == (1u << (k - 2))) {
+            p->fact = 1;
+            p->agg = 0;
+        }
     }
     return GJ_OK;
 }
