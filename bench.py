@@ -7,9 +7,10 @@ build the forward and reverse indices from the device-resident edge list
 relation of Section 5.4), then count and checksum the triangle, diamond and
 4-clique queries in one persistent launch of the fused engine. The diamond
 runs in the attribute order a2, a3, a1, a4, whose last two attributes extend
-independently (factorised, Section 5.4: the last level's groups of prefixes
-share their lookups, Section 3.4.2); the 4-clique runs over three triangle
-atoms (triangle indexing, Section 5.4). ``value`` is matches per second
+independently (factorised output, Section 5.4: the a1 extensions of each
+(a2, a3) pair are counted and their hash factors summed, and the pair is
+extended to a4 once); the 4-clique runs over three triangle atoms (triangle
+indexing, Section 5.4). ``value`` is matches per second
 over the step (device-resident inputs, CUDA events on the library's
 stream); ``e2e`` is the same metric through the C ABI with pinned host
 inputs, so every step also copies the edge list in and the counts out.
@@ -546,7 +547,8 @@ def measure_delta(local, scale, batch_sizes, batches, warmup, host_inputs=True, 
                         "warm-up" % (scale, batch_sizes, batches, warmup),
             "inputs": "pinned host memory, copied inside each timed batch" if host_inputs else "device memory",
             "per_size": per_size, "clocks": clk, "gpu_launches": launches,
-            "engine": "level-synchronous delta queries with old/new views, then the commit"}
+            "engine": "delta queries dQ_i with old/new views on the engine chosen by batch size (level-synchronous "
+                      "below 32,768 normalised changes, fused from there), then the commit proportional to the change"}
 
 
 def run_delta(args):
