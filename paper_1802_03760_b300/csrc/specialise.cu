@@ -140,24 +140,43 @@ __global__ void k_tri_tab_sizes(const int64_t* __restrict__ toff, uint64_t m, in
 
 // Fills the hash sets of the long triangle lists, one warp per list (the
 // same layout and probing as the index's sets: linear probing from the first
-// slot of the key's home group of eight).
-__global__ void k_tri_tab_insert(const int64_t* __restrict__ toff, const uint32_t* __restrict__ tn, uint64_t m,
-                                 const int64_t* __restrict__ tab_off, uint32_t* __restrict__ tab) {
-    const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+// slot of the key's home group of eight). A set of up to TAB_SMEM slots is
+// built in the warp's shared memory and written out whole with 16-byte
+// stores; larger sets are filled in place with global atomics.
+constexpr int TTW = 4;               // warps per block of the insert kernel
+constexpr uint32_t TAB_SMEM = 2048;  // slots of a warp's shared-memory set
+__global__ void __launch_bounds__(TTW * 32) k_tri_tab_insert(const int64_t* __restrict__ toff,
+                                                             const uint32_t* __restrict__ tn, uint64_t m,
+                                                             const int64_t* __restrict__ tab_off,
+                                                             uint32_t* __restrict__ tab) {
+    __shared__ __align__(16) uint32_t s_tab[TTW][TAB_SMEM];
+    const uint64_t warps = (uint64_t)gridDim.x * TTW;
     const int lane = threadIdx.x & 31;
-    for (uint64_t e = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); e < m; e += warps) {
+    uint32_t* st = s_tab[threadIdx.x >> 5];
+    for (uint64_t e = (uint64_t)blockIdx.x * TTW + (threadIdx.x >> 5); e < m; e += warps) {
         const int64_t a = toff[e];
         const uint32_t len = (uint32_t)(toff[e + 1] - a);
         if (len < GJ_HASH_MIN_DEG) continue;
-        const uint32_t bits = gj_tab_bits(len), mask = (1u << bits) - 1u;
-        uint32_t* t = tab + tab_off[e];
+        const uint32_t bits = gj_tab_bits(len), mask = (1u << bits) - 1u, size = 1u << bits;
+        uint32_t* t = tab + tab_off[e];  // 128-byte aligned, size a multiple of 32 slots
+        uint32_t* dst = size <= TAB_SMEM ? st : t;
+        if (size <= TAB_SMEM) {
+            for (uint32_t i = lane; i < size; i += 32) st[i] = GJ_EMPTY;
+            __syncwarp();
+        }
         for (uint32_t i = lane; i < len; i += 32) {
             const uint32_t x = tn[a + i];
             uint32_t h = gj_tab_start(x, bits);
             for (uint32_t probe = 0; probe <= mask; probe++) {
-                if (atomicCAS(t + h, GJ_EMPTY, x) == GJ_EMPTY) break;
+                if (atomicCAS(dst + h, GJ_EMPTY, x) == GJ_EMPTY) break;
                 h = (h + 1u) & mask;
             }
+        }
+        if (size <= TAB_SMEM) {
+            __syncwarp();
+            for (uint32_t i = 4 * lane; i < size; i += 128)
+                *reinterpret_cast<uint4*>(t + i) = *reinterpret_cast<const uint4*>(st + i);
+            __syncwarp();
         }
     }
 }
@@ -225,7 +244,7 @@ static int tri_tables(gj_ctx* ctx, uint64_t m, gj_tri& t) {
     GJ_CUDA_TRY(ctx, gj_malloc(ctx, &t.tab, sizeof(uint32_t) * (size_t)(tsz ? tsz : 1)));
     if (tsz > 0) {
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(t.tab, 0xff, sizeof(uint32_t) * (size_t)tsz, st));
-        k_tri_tab_insert<<<(unsigned)ctx->sm_count * 8, 256, 0, st>>>(t.off, t.nbr, m, t.tab_off, t.tab);
+        k_tri_tab_insert<<<(unsigned)ctx->sm_count * 16, TTW * 32, 0, st>>>(t.off, t.nbr, m, t.tab_off, t.tab);
         GJ_LAUNCHED(ctx);
     }
     GJ_CUDA_TRY(ctx, cudaGetLastError());
