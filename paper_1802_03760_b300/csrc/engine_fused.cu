@@ -181,6 +181,47 @@ __device__ __forceinline__ void member32x2(const uint32_t* __restrict__ a, uint3
     k1 = k1 && f1 == e1;
 }
 
+// Membership of e0 and e1 in two different lists, each given as a hash set
+// (t != null, len >= GJ_HASH_MIN_DEG) or a short sorted list p[0, len) with
+// len < GJ_HASH_MIN_DEG; the two tests' loads are interleaved. k0 / k1 enter
+// as "test this one" and leave as the answers.
+__device__ __forceinline__ void member_pair(const uint32_t* t0, const uint32_t* p0, uint32_t len0, uint32_t e0,
+                                            bool& k0, const uint32_t* t1, const uint32_t* p1, uint32_t len1,
+                                            uint32_t e1, bool& k1) {
+    bool r0 = false, r1 = false;
+    // hash sets: group by group from each key's home group
+    bool a0 = k0 && t0, a1 = k1 && t1;
+    const uint32_t b0 = a0 ? gj_tab_bits(len0) : 0u, b1 = a1 ? gj_tab_bits(len1) : 0u;
+    uint32_t g0 = a0 ? gj_tab_start(e0, b0) : 0u, g1 = a1 ? gj_tab_start(e1, b1) : 0u;
+    while (a0 || a1) {
+        bool hit0 = false, emp0 = false, hit1 = false, emp1 = false;
+        if (a0) gj_tab_group(t0, g0, e0, hit0, emp0);
+        if (a1) gj_tab_group(t1, g1, e1, hit1, emp1);
+        r0 |= hit0;
+        r1 |= hit1;
+        a0 = a0 && !hit0 && !emp0;
+        a1 = a1 && !hit1 && !emp1;
+        g0 = (g0 + 8u) & ((1u << b0) - 1u);
+        g1 = (g1 + 8u) & ((1u << b1) - 1u);
+    }
+    // short sorted lists: four halving steps over [0, len < 16) (lower bound), then one compare
+    const bool s0 = k0 && !t0 && len0, s1 = k1 && !t1 && len1;
+    if (s0 || s1) {
+        uint32_t q0 = 0, q1 = 0;
+#pragma unroll
+        for (uint32_t st = 8; st; st >>= 1) {
+            const bool c0 = s0 && q0 + st <= len0, c1 = s1 && q1 + st <= len1;
+            const uint32_t v0 = c0 ? __ldg(p0 + q0 + st - 1) : 0u, v1 = c1 ? __ldg(p1 + q1 + st - 1) : 0u;
+            if (c0 && v0 < e0) q0 += st;
+            if (c1 && v1 < e1) q1 += st;
+        }
+        if (s0) r0 = q0 < len0 && __ldg(p0 + q0) == e0;
+        if (s1) r1 = q1 < len1 && __ldg(p1 + q1) == e1;
+    }
+    k0 = r0;
+    k1 = r1;
+}
+
 // Two membership tests against the same hash set (groups of eight slots,
 // as in gj_tab_member), their loads interleaved.
 __device__ __forceinline__ void tab_member2(const uint32_t* __restrict__ tab, uint32_t bits, uint32_t e0, bool& k0,
@@ -848,6 +889,50 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     cur = c0 + r;
                     continue;
                 }
+                if (EXT && !DELTA && last && nb == 2) {
+                    // Last level with the kept second list, candidates of several
+                    // short prefixes: two per lane (t and t + 32), each resolved to
+                    // its prefix by binary search, their probes interleaved.
+                    const uint64_t t0 = cur + lane, t1 = cur + 32 + lane;
+                    bool k0 = t0 < tot, k1 = t1 < tot;
+                    uint32_t lo0 = ip, hi0 = nj, lo1 = ip, hi1 = nj;  // last i with cs[i] <= t
+                    while (hi0 - lo0 > 1 || hi1 - lo1 > 1) {
+                        if (hi0 - lo0 > 1) {
+                            const uint32_t mid = (lo0 + hi0) >> 1;
+                            if (cs[mid] <= t0) lo0 = mid; else hi0 = mid;
+                        }
+                        if (hi1 - lo1 > 1) {
+                            const uint32_t mid = (lo1 + hi1) >> 1;
+                            if (cs[mid] <= t1) lo1 = mid; else hi1 = mid;
+                        }
+                    }
+                    const uint32_t i0 = lo0, i1 = lo1;
+                    ip = __shfl_sync(0xffffffffu, i1, 31);  // the next step starts in or after it
+                    const uint32_t e0 = k0 ? __ldg(mptr[i0] + (t0 - cs[i0])) : 0u;
+                    const uint32_t e1 = k1 ? __ldg(mptr[i1] + (t1 - cs[i1])) : 0u;
+                    if (P.nlt[j]) {
+                        k0 = k0 && gj_lt_ok(P, j, e0, [&](uint32_t p) { return tup[p * FC + i0]; });
+                        k1 = k1 && gj_lt_ok(P, j, e1, [&](uint32_t p) { return tup[p * FC + i1]; });
+                    }
+                    const uint32_t* const* olp = reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT));
+                    const uint32_t* const* olt = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT));
+                    const uint32_t* oll = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT));
+                    member_pair(olt[i0], olp[i0], oll[i0], e0, k0, olt[i1], olp[i1], oll[i1], e1, k1);
+                    if (k0) chk += hpre[i0] * gj_hf(a_new, e0);
+                    if (k1) chk += hpre[i1] * gj_hf(a_new, e1);
+                    if (agg || factl) {
+                        // weighted rows: aggregated groups, or factorised parents
+                        const uint32_t w0 = k0 ? (agg ? grp[i0] : tup[(j - 1) * FC + i0]) : 0u;
+                        const uint32_t w1 = k1 ? (agg ? grp[i1] : tup[(j - 1) * FC + i1]) : 0u;
+                        unsigned long long w = (unsigned long long)w0 + w1;
+                        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                        cnt += w;
+                    } else {
+                        cnt += __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                    }
+                    cur += 64;
+                    continue;
+                }
                 const uint64_t t = cur + lane;
                 bool keep = t < tot;
                 const bool uni = !(ip + 1 < nj && cs[ip + 1] < cur + 32);
@@ -860,6 +945,8 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         if (cs[mid] <= t) lo = mid; else hi = mid;
                     }
                     i = lo;
+                    // the next step starts at or after the last lane's prefix
+                    ip = __shfl_sync(0xffffffffu, i, 31);
                 }
                 uint32_t e = 0;
                 int8_t sg = 1;
