@@ -94,6 +94,22 @@ void finish(gj_server* S, Request* r, int status) {
     r->done = true;
 }
 
+// A retired index that no wave reads any more becomes the graph's spare
+// arrays (the next commit writes the next version into them) when it has
+// none; otherwise it is freed. Reusing it avoids a cudaFree, which would
+// wait for every wave in flight, and the next commit's allocations.
+void keep_or_release(gj_graph* g, Retired& rt) {
+    if (!g->spare_fwd.off && !g->spare_rev.off) {
+        g->spare_fwd = rt.fwd;
+        g->spare_rev = rt.rev;
+    } else {
+        gj_csr_release(rt.fwd);
+        gj_csr_release(rt.rev);
+    }
+    rt.fwd = gj_csr{};
+    rt.rev = gj_csr{};
+}
+
 // Completes the waves whose launch finished; frees retired indices no wave reads.
 void reap(gj_server* S) {
     for (size_t i = 0; i < S->inflight.size();) {
@@ -149,8 +165,7 @@ void reap(gj_server* S) {
             i++;
             continue;
         }
-        gj_csr_release(rt.fwd);
-        gj_csr_release(rt.rev);
+        keep_or_release(S->g, rt);
         std::vector<cudaEvent_t> ws = rt.waits;
         S->retired.erase(S->retired.begin() + i);
         for (cudaEvent_t e : ws) {
@@ -266,8 +281,7 @@ bool run_batch(gj_server* S) {
         if (rt.fwd.off) {
             for (Wave* w : S->inflight) rt.waits.push_back(w->done);
             if (rt.waits.empty()) {
-                gj_csr_release(rt.fwd);
-                gj_csr_release(rt.rev);
+                keep_or_release(g, rt);
             } else {
                 S->retired.push_back(rt);
             }
