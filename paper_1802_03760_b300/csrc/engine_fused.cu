@@ -134,8 +134,20 @@ __host__ __device__ __forceinline__ uint32_t off_olp(uint32_t kmax, bool d, bool
 __host__ __device__ __forceinline__ uint32_t off_olt(uint32_t kmax, bool d, bool x) { return off_olp(kmax, d, x) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_oll(uint32_t kmax, bool d, bool x) { return off_olt(kmax, d, x) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_grp(uint32_t kmax, bool d, bool x) { return off_oll(kmax, d, x) + FC * 4; }
+// Delta plans: the other bindings' views of the prefix that a run of
+// single-prefix steps extends (committed list or hash set, and the batch's
+// inserts and deletes of its vertex), computed once for the run.
+struct DViewCache {
+    const uint32_t* cp[2];  // committed list, or its hash set when cbits > 0
+    const uint32_t* ins[2];
+    const uint32_t* del[2];
+    uint32_t cl[2], cbits[2], nins[2], ndel[2];
+};
+__host__ __device__ __forceinline__ uint32_t off_dvc(uint32_t kmax, bool d, bool x) {
+    return off_hpre(kmax, d, x) + FC * 8 + (x ? ALIGN16(FC * 8 + FC * 8 + FC * 4 + FC) : 0);
+}
 __host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d, bool x) {
-    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : off_hpre(kmax, d, x) + FC * 8 + (x ? ALIGN16(FC * 8 + FC * 8 + FC * 4 + FC) : 0);
+    return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : off_dvc(kmax, d, x) + (d ? ALIGN16(sizeof(DViewCache)) : 0);
 }
 
 __device__ __forceinline__ void stat_add(unsigned long long* s, int which, int j, unsigned long long v) {
@@ -745,6 +757,28 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             const uint32_t* ob[MAXO];  // the list, or its hash set when obits > 0
             uint32_t ol[MAXO], obits[MAXO];
             uint32_t cached = 0xffffffffu;
+            uint32_t dcached = 0xffffffffu;  // delta plans: the prefix whose views the cache holds
+            DViewCache* dvc = reinterpret_cast<DViewCache*>(ws + off_dvc(A.kmax, DELTA, EXT));
+            // delta plans: the other views of prefix pi, lane q taking the q-th one
+            auto dcache = [&](uint32_t pi) {
+                const uint32_t b0 = minb[pi];
+                if (lane + 1 < (int)nb) {
+                    const uint32_t b = (uint32_t)lane < b0 ? (uint32_t)lane : (uint32_t)lane + 1;
+                    const uint32_t dir = P.bdir[j][b];
+                    const uint32_t v = tup[P.bpos[j][b] * FC + pi];
+                    const ViewList L = gj_view_list(G, Dv, dir, P.bview[j][b], v);
+                    const bool hs = L.base_len >= GJ_HASH_MIN_DEG;
+                    dvc->cp[lane] = hs ? (dir ? G.rt : G.ft) + __ldg((dir ? G.rto : G.fto) + v) : L.base;
+                    dvc->cbits[lane] = hs ? gj_tab_bits(L.base_len) : 0u;
+                    dvc->cl[lane] = L.base_len;
+                    dvc->ins[lane] = L.ins;
+                    dvc->nins[lane] = L.nins;
+                    dvc->del[lane] = L.del;
+                    dvc->ndel[lane] = L.ndel;
+                }
+                __syncwarp();
+                dcached = pi;
+            };
             uint32_t lo_in = 0;         // the cached prefix's inequality bounds: lo_in <= e < hi_ex
             uint64_t hi_ex = 1ull << 32;
             // the other binding lists and the inequality bounds of prefix pi, in registers
@@ -889,6 +923,51 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     cur = c0 + r;
                     continue;
                 }
+                if (DELTA && last && nb <= 3 && !(ip + 1 < nj && cs[ip + 1] < cur + 64)) {
+                    // Delta plans, last level, next 64 candidates all in prefix ip:
+                    // two per lane, the other views cached once for the run, the
+                    // committed-list probes of the two candidates interleaved.
+                    if (ip != dcached) dcache(ip);
+                    const uint64_t c0 = cs[ip];
+                    const uint32_t r0 = (uint32_t)(cur - c0) + lane, r1 = r0 + 32;
+                    bool k0 = cur + lane < tot, k1 = cur + 32 + lane < tot;
+                    const uint32_t blen = reinterpret_cast<const uint32_t*>(ws + off_dblen(j, EXT))[ip];
+                    const uint32_t mdel = reinterpret_cast<const uint32_t*>(ws + off_dndel(j, EXT))[ip];
+                    const uint32_t* mins = reinterpret_cast<const uint32_t* const*>(ws + off_dins(j, EXT))[ip];
+                    const uint32_t* mdl = reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j, EXT))[ip];
+                    const uint32_t* ml = mptr[ip];
+                    uint32_t e0 = 0, e1 = 0;
+                    if (k0) e0 = r0 < blen ? __ldg(ml + r0) : __ldg(mins + (r0 - blen));
+                    if (k1) e1 = r1 < blen ? __ldg(ml + r1) : __ldg(mins + (r1 - blen));
+                    if (mdel) {  // committed entries deleted in the min list's view
+                        if (k0 && r0 < blen) k0 = !gj_contains(mdl, mdel, e0);
+                        if (k1 && r1 < blen) k1 = !gj_contains(mdl, mdel, e1);
+                    }
+                    if (EXT && P.nlt[j]) {
+                        k0 = k0 && gj_lt_ok(P, j, e0, [&](uint32_t p) { return tup[p * FC + ip]; });
+                        k1 = k1 && gj_lt_ok(P, j, e1, [&](uint32_t p) { return tup[p * FC + ip]; });
+                    }
+                    for (uint32_t q = 0; q + 1 < nb; q++) {
+                        // inserted in this view: a member; deleted: not; else the committed list
+                        const bool in0 = k0 && dvc->nins[q] && gj_contains(dvc->ins[q], dvc->nins[q], e0);
+                        const bool in1 = k1 && dvc->nins[q] && gj_contains(dvc->ins[q], dvc->nins[q], e1);
+                        const bool de0 = k0 && !in0 && dvc->ndel[q] && gj_contains(dvc->del[q], dvc->ndel[q], e0);
+                        const bool de1 = k1 && !in1 && dvc->ndel[q] && gj_contains(dvc->del[q], dvc->ndel[q], e1);
+                        bool c0 = k0 && !in0 && !de0, c1 = k1 && !in1 && !de1;
+                        const uint32_t* tb = dvc->cbits[q] ? dvc->cp[q] : nullptr;
+                        member_pair(tb, dvc->cp[q], dvc->cl[q], e0, c0, tb, dvc->cp[q], dvc->cl[q], e1, c1);
+                        k0 = in0 || c0;
+                        k1 = in1 || c1;
+                    }
+                    const int8_t sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[ip];
+                    const uint64_t hp = hpre[ip];
+                    uint64_t h = (k0 ? hp * gj_hf(a_new, e0) : 0ull) + (k1 ? hp * gj_hf(a_new, e1) : 0ull);
+                    chk += sg > 0 ? h : 0ull - h;
+                    const int c2 = __popc(__ballot_sync(0xffffffffu, k0)) + __popc(__ballot_sync(0xffffffffu, k1));
+                    cnt += sg > 0 ? (unsigned long long)c2 : 0ull - (unsigned long long)c2;
+                    cur += 64;
+                    continue;
+                }
                 if (EXT && !DELTA && last && nb == 2) {
                     // Last level with the kept second list, candidates of several
                     // short prefixes: two per lane (t and t + 32), each resolved to
@@ -964,6 +1043,21 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                             e = __ldg(reinterpret_cast<const uint32_t* const*>(ws + off_dins(j, EXT))[i] + (r - blen));
                         }
                         sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[i];
+                    }
+                    if (uni && nb <= 3) {
+                        // every candidate of the step is prefix ip's: its other views
+                        // are looked up once per run (lane q takes the q-th one)
+                        if (ip != dcached) dcache(ip);
+                        for (uint32_t q = 0; q + 1 < nb && keep; q++) {
+                            if (dvc->nins[q] && gj_contains(dvc->ins[q], dvc->nins[q], e)) continue;  // inserted: a member
+                            if (dvc->ndel[q] && gj_contains(dvc->del[q], dvc->ndel[q], e)) {
+                                keep = false;  // deleted in this view
+                                continue;
+                            }
+                            keep = dvc->cbits[q] ? gj_tab_member(dvc->cp[q], dvc->cbits[q], e)
+                                                 : gj_contains(dvc->cp[q], dvc->cl[q], e);
+                        }
+                    } else if (keep) {
                         const uint32_t b0 = minb[i];
                         for (uint32_t b = 0; b < nb && keep; b++) {
                             if (b == b0) continue;
