@@ -548,7 +548,7 @@ def measure_delta(local, scale, batch_sizes, batches, warmup, host_inputs=True, 
             "inputs": "pinned host memory, copied inside each timed batch" if host_inputs else "device memory",
             "per_size": per_size, "clocks": clk, "gpu_launches": launches,
             "engine": "delta queries dQ_i with old/new views on the engine chosen by batch size (level-synchronous "
-                      "below 32,768 normalised changes, fused from there), then the commit proportional to the change"}
+                      "below 8,192 normalised changes, fused from there), then the commit proportional to the change"}
 
 
 def run_delta(args):

@@ -86,7 +86,7 @@ enum {
 };
 
 /* Option flags for the delta queries of update batches. By default a batch
- * of fewer than 32768 normalised changes runs on the level-synchronous
+ * of fewer than 8192 normalised changes runs on the level-synchronous
  * engine (which spreads a small batch's fan-out over the whole GPU at once)
  * and a larger one on the fused engine (which balances its work by
  * donation). GJ_FLAG_DELTA_FUSED / GJ_FLAG_DELTA_PLAIN force one of them. */
@@ -266,7 +266,8 @@ int gj_count_many_ex(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint32
 
 /* Launch settings of a context. */
 typedef struct {
-    uint32_t seed_chunk;           /* fused engine: seeds a warp takes per grab (32..4096, multiple of 32) */
+    uint32_t seed_chunk;           /* fused engine: seeds a warp takes per grab (8..4096, multiple of 8;
+                                    * delta launches take at most 8) */
     uint32_t blocks_per_sm;        /* fused engine: resident blocks per SM, 0 = as many as fit */
     uint64_t prefix_buffer_bytes;  /* level-synchronous engine: prefix-buffer budget, 0 = 512 MiB */
     double fused_ms, plain_ms;     /* gj_autotune: the sample's time with the chosen settings */
@@ -302,7 +303,7 @@ typedef struct {
 int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
 /* Replaces the context's settings (fused_ms and plain_ms are ignored); results
  * never depend on them (except for the failure-injection field). Errors:
- * GJ_E_INVALID (seed_chunk out of range or not a multiple of 32, budget under
+ * GJ_E_INVALID (seed_chunk out of range or not a multiple of 8, budget under
  * 1 MiB, donation > 2, fault > 2). */
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
 /*

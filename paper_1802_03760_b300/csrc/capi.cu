@@ -496,7 +496,7 @@ int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out) {
 }
 
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t) {
-    if (!ctx || !t || t->seed_chunk < 32 || t->seed_chunk > 4096 || t->seed_chunk % 32) return GJ_E_INVALID;
+    if (!ctx || !t || t->seed_chunk < 8 || t->seed_chunk > 4096 || t->seed_chunk % 8) return GJ_E_INVALID;
     if (t->prefix_buffer_bytes && t->prefix_buffer_bytes < (1ull << 20)) return GJ_E_INVALID;
     if (t->donation > 2 || t->fault > GJ_FAULT_ALLOC) return GJ_E_INVALID;
     if (t->fault == GJ_FAULT_NARROW_VIEW && !GJ_CHECKED_BUILD) {

@@ -26,7 +26,8 @@ namespace {
 constexpr int FC = 64;          // frontier capacity per level per warp (2 B')
 constexpr int FT = 32;          // B': descend once a level holds this many prefixes
 constexpr int FW = 8;           // warps per block
-constexpr int SEED_CHUNK = 32;  // default seeds per grab (a multiple of 32; tunable per launch)
+constexpr int SEED_CHUNK = 32;  // default seeds per grab (a multiple of 8; tunable per launch)
+constexpr uint32_t DELTA_CHUNK = 8;  // most seeds per grab in delta launches
 
 // A batch of up to FC prefixes of one plan and level that a busy warp hands
 // to idle warps (the balance step of Section 3.4 at warp granularity).
@@ -79,7 +80,7 @@ struct FusedArgs {
     unsigned long long* ovf;    // set when a static count passes 2^63 - 1 (may be null)
     DeltaView D;                // delta plans: the batch's per-direction insert/delete arrays
     DeltaBatch B;               // delta plans: the batch's signed changes (the seeds)
-    uint32_t chunk = SEED_CHUNK;  // seeds a warp takes per grab (multiple of 32)
+    uint32_t chunk = SEED_CHUNK;  // seeds a warp takes per grab (multiple of 8)
     DonationQueue Q;
     uint64_t wait_ns = 0;       // bound of the end-of-launch wait without progress
 };
@@ -668,12 +669,14 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 __syncwarp();
                 k = P.k;
             }
+            // up to 32 seeds of the grabbed range (fewer when a grab is smaller)
+            const uint64_t span = gend - g < 32 ? gend - g : 32;
             const uint64_t s = g - A.qbase[q] + lane;
-            bool keep = (int64_t)s < A.seed_n[q];
-            gpos = g + 32;
+            bool keep = (int64_t)s < A.seed_n[q] && (uint64_t)lane < span;
+            gpos = g + span;
             if (lane == 0) {
                 int64_t left = A.seed_n[q] - (int64_t)(g - A.qbase[q]);
-                if (left > 0) stat_add(A.stats, 4, 0, (unsigned long long)(left < 32 ? left : 32));
+                if (left > 0) stat_add(A.stats, 4, 0, (unsigned long long)((uint64_t)left < span ? left : span));
             }
             uint32_t x0 = 0, x1 = 0;
             int8_t sg = 1;
@@ -1695,12 +1698,15 @@ int gj_engine_fused_delta(gj_ctx* ctx, const gj_graph* g, const DeltaBatch& batc
         for (uint32_t q = 0; q < nc; q++) kmax = plans[c0 + q].k > kmax ? plans[c0 + q].k : kmax;
         GJ_CUDA_TRY(ctx, cudaMemcpyAsync(d_plans, plans + c0, sizeof(Plan) * nc, cudaMemcpyHostToDevice, st));
         GJ_CUDA_TRY(ctx, cudaMemsetAsync(counts_d, 0, 8 * (2 * (size_t)nc + 1 + NSTAT), st));
-        k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n, ctx->seed_chunk);
+        // a batch's signed seeds are few and each fans out through hub lists:
+        // warps take at most DELTA_CHUNK of them per grab, so more warps start
+        const uint32_t chunk = ctx->seed_chunk < DELTA_CHUNK ? ctx->seed_chunk : DELTA_CHUNK;
+        k_seed_ranges<<<1, 1, 0, st>>>(d_plans, nc, G, 0, 0, seed_lo, seed_n, qbase, batch.n, chunk);
         GJ_LAUNCHED(ctx);
         FusedCfg cfg;
         GJ_TRY(fused_cfg<true>(ctx, kmax, plans + c0, nc, &cfg));
         FusedArgs A{G, d_plans, nc, kmax, qbase, seed_lo, seed_n, next, counts_d, chks_d, stats, nullptr};
-        A.chunk = ctx->seed_chunk;
+        A.chunk = chunk;
         A.wait_ns = gj_wait_ns(ctx);
         A.D = batch.view;
         A.B = batch;

@@ -329,7 +329,7 @@ int gj_check_status(gj_ctx* ctx);
 // Engine of a batch's delta queries: the level-synchronous one spreads a
 // small batch's fan-out over the whole GPU at once, the fused one balances
 // a large batch's work better; GJ_FLAG_DELTA_PLAIN / _FUSED force either.
-constexpr uint64_t GJ_DELTA_FUSED_MIN = 32768;  // normalised changes from which the fused engine runs
+constexpr uint64_t GJ_DELTA_FUSED_MIN = 8192;  // normalised changes from which the fused engine runs
 inline uint32_t gj_delta_engine(const gj_ctx* ctx, uint64_t changes) {
     if (ctx->opt.flags & GJ_FLAG_DELTA_PLAIN) return GJ_ENGINE_PLAIN;
     if (ctx->opt.flags & GJ_FLAG_DELTA_FUSED) return GJ_ENGINE_FUSED;

@@ -35,7 +35,8 @@ def test_64_queries_one_launch(setup):
     assert list(zip(c, h)) == want
 
 
-@pytest.mark.parametrize("chunk,bps,donation", [(64, 0, 0), (128, 1, 1), (256, 2, 2), (32, 1, 1), (32, 0, 1)])
+@pytest.mark.parametrize("chunk,bps,donation", [(64, 0, 0), (128, 1, 1), (256, 2, 2), (32, 1, 1), (32, 0, 1),
+                                                (8, 0, 1), (16, 0, 0), (40, 1, 1)])
 def test_fused_settings_do_not_change_results(setup, chunk, bps, donation):
     """Seeds per grab, blocks per SM and work donation (1 = donate whenever a
     queue slot is free, which exercises the queue on every descent) must not
@@ -81,4 +82,4 @@ def test_autotune_picks_valid_settings(setup):
     assert list(zip(*gj.count_many(g, qs))) == want
     gj.set_tuning(ctx)
     with pytest.raises(gj.GJError):
-        gj.set_tuning(ctx, seed_chunk=48)
+        gj.set_tuning(ctx, seed_chunk=44)
