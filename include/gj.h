@@ -304,12 +304,12 @@ int gj_get_tuning(const gj_ctx* ctx, gj_tuning* out);
 /* Replaces the context's settings (fused_ms and plain_ms are ignored); results
  * never depend on them (except for the failure-injection field). Errors:
  * GJ_E_INVALID (seed_chunk out of range or not a multiple of 8, budget under
- * 1 MiB, donation > 2, fault > 2). */
+ * 1 MiB, donation > 2, fault > 4). */
 int gj_set_tuning(gj_ctx* ctx, const gj_tuning* t);
 /*
  * Chooses the context's launch settings by timing the given queries on the
  * first-attribute range [v_lo, v_hi) of g (a sample of the workload): seeds
- * per grab in {32, 64, 128, 256} x {all, all but one} resident blocks per SM
+ * per grab in {8, 32, 128} x {all, all but one} resident blocks per SM
  * x donation when warps idle or whenever a queue slot is free for the fused
  * engine, and a prefix-buffer budget in {64 MiB, 256 MiB,
  * 1 GiB, 2 GiB} up to prefix_cap_bytes (0 = 2 GiB) for the level-synchronous

@@ -562,7 +562,7 @@ int autotune_sweep(gj_graph* g, const gj_query* const* qs, uint32_t nq, uint64_t
     }
     double best_f = 1e300;
     uint32_t best_chunk = 32, best_bps = 0, best_don = 0;
-    for (uint32_t chunk : {32u, 64u, 128u, 256u}) {
+    for (uint32_t chunk : {8u, 32u, 128u}) {
         for (int bps : {0, per_sm_max - 1}) {  // 0: as many blocks as fit
             if (bps < 0) continue;
             for (uint32_t don : {0u, 1u}) {  // donate when warps idle / whenever a slot is free

@@ -75,7 +75,7 @@ def test_sampled_ranges_add_up(setup):
 def test_autotune_picks_valid_settings(setup):
     ctx, g, qs, want, n = setup
     t = gj.autotune(g, qs[:10], v_range=(0, n // 4), prefix_cap_bytes=256 << 20)
-    assert t["seed_chunk"] in (32, 64, 128, 256)
+    assert t["seed_chunk"] in (8, 32, 128)
     assert t["prefix_buffer_bytes"] in (64 << 20, 256 << 20)
     assert t["fused_ms"] > 0 and t["plain_ms"] > 0
     assert gj.get_tuning(ctx)["seed_chunk"] == t["seed_chunk"]
