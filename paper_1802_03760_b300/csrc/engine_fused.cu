@@ -1052,13 +1052,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         // are looked up once per run (lane q takes the q-th one)
                         if (ip != dcached) dcache(ip);
                         for (uint32_t q = 0; q + 1 < nb && keep; q++) {
-                            if (dvc->nins[q] && gj_contains(dvc->ins[q], dvc->nins[q], e)) continue;  // inserted: a member
-                            if (dvc->ndel[q] && gj_contains(dvc->del[q], dvc->ndel[q], e)) {
-                                keep = false;  // deleted in this view
-                                continue;
-                            }
-                            keep = dvc->cbits[q] ? gj_tab_member(dvc->cp[q], dvc->cbits[q], e)
-                                                 : gj_contains(dvc->cp[q], dvc->cl[q], e);
+                            // committed member unless deleted; otherwise only if inserted
+                            const bool c = dvc->cbits[q] ? gj_tab_member(dvc->cp[q], dvc->cbits[q], e)
+                                                         : gj_contains(dvc->cp[q], dvc->cl[q], e);
+                            keep = c ? !(dvc->ndel[q] && gj_contains(dvc->del[q], dvc->ndel[q], e))
+                                     : (dvc->nins[q] && gj_contains(dvc->ins[q], dvc->nins[q], e));
                         }
                     } else if (keep) {
                         const uint32_t b0 = minb[i];

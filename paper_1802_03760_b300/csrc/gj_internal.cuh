@@ -603,19 +603,21 @@ __device__ __forceinline__ ViewList gj_view_list(const GraphView& G, const Delta
     return L;
 }
 
-// Membership of x in v's list under a view: the batch's changes of v
-// first (they are normalised: inserts are absent from the committed list,
-// deletes present), then the committed index.
+// Membership of x in v's list under a view: the committed index first,
+// then one of the batch's change lists of v. The batch is normalised
+// (inserts are absent from the committed list, deletes present), so a
+// committed member is a member unless deleted, and any other x only if
+// inserted.
 __device__ __forceinline__ bool gj_view_member(const GraphView& G, const DeltaView* D, uint32_t dir, uint32_t view,
                                                uint32_t v, uint32_t x) {
     if (!GJ_CHECK(G.chk, v < G.n, GJ_SITE_VERTEX, v)) return false;
+    const bool c = dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
     if (view == GJ_VIEW_NEW && D) {
         const DeltaSide& S = dir ? D->rev : D->fwd;
         const uint4 r = gj_delta_ranges(S, v);
-        if (gj_contains(S.ins_nbr + r.x, r.y - r.x, x)) return true;
-        if (gj_contains(S.del_nbr + r.z, r.w - r.z, x)) return false;
+        return c ? !gj_contains(S.del_nbr + r.z, r.w - r.z, x) : gj_contains(S.ins_nbr + r.x, r.y - r.x, x);
     }
-    return dir ? gj_list_member(G.ro, G.rn, G.rto, G.rt, v, x) : gj_list_member(G.fo, G.fn, G.fto, G.ft, v, x);
+    return c;
 }
 
 // The list a binding of a plan level reads for one prefix (static plans):
