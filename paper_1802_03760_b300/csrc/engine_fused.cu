@@ -131,9 +131,9 @@ __host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j, bool x) { ret
 __host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j, bool x) { return off_dndel(j, x) + FC * 4; }
 // the last-level block, after the levels of the launch's longest query
 __host__ __device__ __forceinline__ uint32_t off_hpre(uint32_t kmax, bool d, bool) { return lvl_base(kmax, d); }
+// the kept second list: its hash set when it has one (length >= GJ_HASH_MIN_DEG), else the sorted list
 __host__ __device__ __forceinline__ uint32_t off_olp(uint32_t kmax, bool d, bool x) { return off_hpre(kmax, d, x) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_olt(uint32_t kmax, bool d, bool x) { return off_olp(kmax, d, x) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_oll(uint32_t kmax, bool d, bool x) { return off_olt(kmax, d, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_oll(uint32_t kmax, bool d, bool x) { return off_olp(kmax, d, x) + FC * 8; }
 __host__ __device__ __forceinline__ uint32_t off_grp(uint32_t kmax, bool d, bool x) { return off_oll(kmax, d, x) + FC * 4; }
 // Delta plans: the other bindings' views of the prefix that a run of
 // single-prefix steps extends (committed list or hash set, and the batch's
@@ -145,7 +145,7 @@ struct DViewCache {
     uint32_t cl[2], cbits[2], nins[2], ndel[2];
 };
 __host__ __device__ __forceinline__ uint32_t off_dvc(uint32_t kmax, bool d, bool x) {
-    return off_hpre(kmax, d, x) + FC * 8 + (x ? ALIGN16(FC * 8 + FC * 8 + FC * 4 + FC) : 0);
+    return off_hpre(kmax, d, x) + FC * 8 + (x ? ALIGN16(FC * 8 + FC * 4 + FC) : 0);
 }
 __host__ __device__ __forceinline__ uint32_t warp_bytes(uint32_t kmax, bool d, bool x) {
     return kmax <= 2 ? PLAN_BYTES + SCAL_BYTES : off_dvc(kmax, d, x) + (d ? ALIGN16(sizeof(DViewCache)) : 0);
@@ -421,8 +421,7 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         }
                     }
                     if (keep_other) {
-                        reinterpret_cast<const uint32_t**>(ws + off_olp(A.kmax, DELTA, EXT))[i] = other.p;
-                        reinterpret_cast<const uint32_t**>(ws + off_olt(A.kmax, DELTA, EXT))[i] = other.bits ? other.tab : nullptr;
+                        reinterpret_cast<const uint32_t**>(ws + off_olp(A.kmax, DELTA, EXT))[i] = other.bits ? other.tab : other.p;
                         reinterpret_cast<uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[i] = other.len;
                     }
                     all2 += best;
@@ -787,10 +786,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
             // the other binding lists and the inequality bounds of prefix pi, in registers
             auto cache_prefix = [&](uint32_t pi) {
                 if (EXT && last && nb == 2) {  // the other list, kept by the count step
-                    const uint32_t* t = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT))[pi];
                     ol[0] = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[pi];
-                    ob[0] = t ? t : reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[pi];
-                    obits[0] = t ? gj_tab_bits(ol[0]) : 0u;
+                    ob[0] = reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[pi];
+                    obits[0] = ol[0] >= GJ_HASH_MIN_DEG ? gj_tab_bits(ol[0]) : 0u;
                 } else {
                     const uint32_t b0 = minb[pi];
                     uint32_t o = 0;
@@ -997,9 +995,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         k1 = k1 && gj_lt_ok(P, j, e1, [&](uint32_t p) { return tup[p * FC + i1]; });
                     }
                     const uint32_t* const* olp = reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT));
-                    const uint32_t* const* olt = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT));
                     const uint32_t* oll = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT));
-                    member_pair(olt[i0], olp[i0], oll[i0], e0, k0, olt[i1], olp[i1], oll[i1], e1, k1);
+                    const uint32_t l0 = oll[i0], l1 = oll[i1];
+                    member_pair(l0 >= GJ_HASH_MIN_DEG ? olp[i0] : nullptr, olp[i0], l0, e0, k0,
+                                l1 >= GJ_HASH_MIN_DEG ? olp[i1] : nullptr, olp[i1], l1, e1, k1);
                     if (k0) chk += hpre[i0] * gj_hf(a_new, e0);
                     if (k1) chk += hpre[i1] * gj_hf(a_new, e1);
                     if (agg || factl) {
@@ -1080,8 +1079,10 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                 } else if (EXT && last && nb == 2) {
                     // the other list, kept by the count step
                     if (keep) {
-                        const uint32_t* t = reinterpret_cast<const uint32_t* const*>(ws + off_olt(A.kmax, DELTA, EXT))[i];
                         const uint32_t len = reinterpret_cast<const uint32_t*>(ws + off_oll(A.kmax, DELTA, EXT))[i];
+                        const uint32_t* t = len >= GJ_HASH_MIN_DEG
+                                                ? reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[i]
+                                                : nullptr;
                         keep = t ? gj_tab_member(t, gj_tab_bits(len), e)
                                  : gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_olp(A.kmax, DELTA, EXT))[i],
                                                len, e);
@@ -1303,6 +1304,17 @@ int fused_cfg_t(gj_ctx* ctx, uint32_t kmax, bool cap, FusedCfg* c) {
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, k_fused<DELTA, EXT>, FW * 32, c->smem));
     if (cap && ctx->blocks_per_sm && (int)ctx->blocks_per_sm < c->per_sm) c->per_sm = (int)ctx->blocks_per_sm;
     if (c->per_sm < 1) c->per_sm = 1;
+    // Ask for the smallest shared-memory carveout that holds the resident
+    // blocks (each also reserves 1 KB), so that the rest of the SM's unified
+    // L1 / shared memory serves as L1 for the probed lists and hash sets.
+    int maxsm = 0;
+    GJ_CUDA_TRY(ctx, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    if (maxsm > 0) {
+        const long need = (long)c->per_sm * (c->smem + 1024);
+        const int pct = (int)((need * 100 + maxsm - 1) / maxsm);
+        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<DELTA, EXT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              pct < 100 ? pct : 100));
+    }
     c->ext = EXT;
     return GJ_OK;
 }
