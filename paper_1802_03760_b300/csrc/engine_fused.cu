@@ -111,8 +111,10 @@ constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
 constexpr uint32_t LVL_FIXED = FC * 8 + ALIGN16((FC + 1) * 8) + ALIGN16(FC);  // mptr + cs + minb
 // Delta plans also keep, per prefix, the new-version parts of the min list
-// (inserts, deletes, committed length) and the seed's sign.
-constexpr uint32_t LVL_DELTA = FC * 8 + FC * 8 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
+// (where its inserts and deletes start in the batch's arrays of the min
+// binding's direction, committed length, number of deletes) and the seed's
+// sign.
+constexpr uint32_t LVL_DELTA = FC * 4 + FC * 4 + FC * 4 + FC * 4 + FC;  // ins, del, base len, ndel, sign
 __host__ __device__ __forceinline__ uint32_t lvl_size_fixed(bool d) { return LVL_FIXED + (d ? ALIGN16(LVL_DELTA) : 0); }
 __host__ __device__ __forceinline__ uint32_t lvl_base(uint32_t j, bool d) {
     // sum over i = 2..j-1 of (FC * i * 4 + fixed part)
@@ -125,8 +127,16 @@ __host__ __device__ __forceinline__ uint32_t off_minb(uint32_t j, bool d, bool x
     return off_cs(j, d, x) + ALIGN16((FC + 1) * 8);
 }
 __host__ __device__ __forceinline__ uint32_t off_dins(uint32_t j, bool x) { return off_minb(j, true, x) + ALIGN16(FC); }
-__host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j, bool x) { return off_dins(j, x) + FC * 8; }
-__host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j, bool x) { return off_ddel(j, x) + FC * 8; }
+__host__ __device__ __forceinline__ uint32_t off_ddel(uint32_t j, bool x) { return off_dins(j, x) + FC * 4; }
+__host__ __device__ __forceinline__ uint32_t off_dblen(uint32_t j, bool x) { return off_ddel(j, x) + FC * 4; }
+
+// The batch's insert and delete arrays of one direction (delta plans).
+__device__ __forceinline__ const uint32_t* dins_base(const DeltaView& D, uint32_t dir) {
+    return dir ? D.rev.ins_nbr : D.fwd.ins_nbr;
+}
+__device__ __forceinline__ const uint32_t* ddel_base(const DeltaView& D, uint32_t dir) {
+    return dir ? D.rev.del_nbr : D.fwd.del_nbr;
+}
 __host__ __device__ __forceinline__ uint32_t off_dndel(uint32_t j, bool x) { return off_dblen(j, x) + FC * 4; }
 __host__ __device__ __forceinline__ uint32_t off_dsg(uint32_t j, bool x) { return off_dndel(j, x) + FC * 4; }
 // the last-level block, after the levels of the launch's longest query
@@ -379,8 +389,11 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     }
                     best = bl.space();
                     bp = bl.base;
-                    reinterpret_cast<const uint32_t**>(ws + off_dins(j, EXT))[i] = bl.ins;
-                    reinterpret_cast<const uint32_t**>(ws + off_ddel(j, EXT))[i] = bl.del;
+                    const uint32_t bdir = P.bdir[j][bi];
+                    reinterpret_cast<uint32_t*>(ws + off_dins(j, EXT))[i] =
+                        bl.nins ? (uint32_t)(bl.ins - dins_base(A.D, bdir)) : 0u;
+                    reinterpret_cast<uint32_t*>(ws + off_ddel(j, EXT))[i] =
+                        bl.ndel ? (uint32_t)(bl.del - ddel_base(A.D, bdir)) : 0u;
                     reinterpret_cast<uint32_t*>(ws + off_dblen(j, EXT))[i] = bl.base_len;
                     reinterpret_cast<uint32_t*>(ws + off_dndel(j, EXT))[i] = bl.ndel;
                 } else {
@@ -934,8 +947,9 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                     bool k0 = cur + lane < tot, k1 = cur + 32 + lane < tot;
                     const uint32_t blen = reinterpret_cast<const uint32_t*>(ws + off_dblen(j, EXT))[ip];
                     const uint32_t mdel = reinterpret_cast<const uint32_t*>(ws + off_dndel(j, EXT))[ip];
-                    const uint32_t* mins = reinterpret_cast<const uint32_t* const*>(ws + off_dins(j, EXT))[ip];
-                    const uint32_t* mdl = reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j, EXT))[ip];
+                    const uint32_t mdir = P.bdir[j][minb[ip]];
+                    const uint32_t* mins = dins_base(A.D, mdir) + reinterpret_cast<const uint32_t*>(ws + off_dins(j, EXT))[ip];
+                    const uint32_t* mdl = ddel_base(A.D, mdir) + reinterpret_cast<const uint32_t*>(ws + off_ddel(j, EXT))[ip];
                     const uint32_t* ml = mptr[ip];
                     uint32_t e0 = 0, e1 = 0;
                     if (k0) e0 = r0 < blen ? __ldg(ml + r0) : __ldg(mins + (r0 - blen));
@@ -1040,9 +1054,12 @@ __global__ void __launch_bounds__(FW * 32, 4) k_fused(FusedArgs A) {
                         if (r < blen) {
                             e = __ldg(mptr[i] + r);
                             if (ndel)
-                                keep = !gj_contains(reinterpret_cast<const uint32_t* const*>(ws + off_ddel(j, EXT))[i], ndel, e);
+                                keep = !gj_contains(ddel_base(A.D, P.bdir[j][minb[i]]) +
+                                                        reinterpret_cast<const uint32_t*>(ws + off_ddel(j, EXT))[i],
+                                                    ndel, e);
                         } else {
-                            e = __ldg(reinterpret_cast<const uint32_t* const*>(ws + off_dins(j, EXT))[i] + (r - blen));
+                            e = __ldg(dins_base(A.D, P.bdir[j][minb[i]]) +
+                                      reinterpret_cast<const uint32_t*>(ws + off_dins(j, EXT))[i] + (r - blen));
                         }
                         sg = reinterpret_cast<const int8_t*>(ws + off_dsg(j, EXT))[i];
                     }
@@ -1304,17 +1321,6 @@ int fused_cfg_t(gj_ctx* ctx, uint32_t kmax, bool cap, FusedCfg* c) {
     GJ_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c->per_sm, k_fused<DELTA, EXT>, FW * 32, c->smem));
     if (cap && ctx->blocks_per_sm && (int)ctx->blocks_per_sm < c->per_sm) c->per_sm = (int)ctx->blocks_per_sm;
     if (c->per_sm < 1) c->per_sm = 1;
-    // Ask for the smallest shared-memory carveout that holds the resident
-    // blocks (each also reserves 1 KB), so that the rest of the SM's unified
-    // L1 / shared memory serves as L1 for the probed lists and hash sets.
-    int maxsm = 0;
-    GJ_CUDA_TRY(ctx, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-    if (maxsm > 0) {
-        const long need = (long)c->per_sm * (c->smem + 1024);
-        const int pct = (int)((need * 100 + maxsm - 1) / maxsm);
-        GJ_CUDA_TRY(ctx, cudaFuncSetAttribute(k_fused<DELTA, EXT>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                              pct < 100 ? pct : 100));
-    }
     c->ext = EXT;
     return GJ_OK;
 }
