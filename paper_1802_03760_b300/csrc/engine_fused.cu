@@ -105,7 +105,11 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // of a two-binding last level [FC] (pointer, hash set, length) and the size
 // of each aggregated group [FC]. A warp finishes a last-level batch before
 // it activates another one, so one block serves every query. Offsets are
-// closed forms so that no per-level table sits in local memory.
+// closed forms so that no per-level table sits in local memory. The
+// footprint is kept small on purpose: the driver gives an SM's unified L1 /
+// shared memory the smallest shared-memory size that holds the resident
+// blocks, and the rest is L1 for the probed lists and hash sets (four
+// extended k = 4 blocks fit 196 KB, leaving about 60 KB of L1).
 constexpr uint32_t ALIGN16(uint32_t b) { return (b + 15u) & ~15u; }
 constexpr uint32_t PLAN_BYTES = ALIGN16(sizeof(Plan));
 constexpr uint32_t SCAL_BYTES = 4 * GJ_MAX_K * 8;
