@@ -11,11 +11,14 @@ relation, factorised output). It shares no code with the CUDA path. This
 module only marshals arguments through ctypes and compiles the C file with
 gcc.
 
-Pins (what fixes the oracle other than itself) live in tests/test_oracle.py:
-brute-force enumeration of V^k on tiny graphs, closed forms on complete
-graphs, traces of adjacency powers on symmetric graphs, the worked example
-of Appendix A, SplitMix64 reference outputs, invariance under attribute
-order, and delta = recount-after minus recount-before.
+Pins (what fixes the oracle other than itself) live in tests/test_oracle.py
+and tests/test_oracle_specialisations.py: brute-force enumeration of V^k on
+tiny graphs, closed forms on complete graphs, traces of adjacency powers on
+symmetric graphs, the worked example of Appendix A, SplitMix64 reference
+outputs, invariance under attribute order, delta = recount-after minus
+recount-before and each delta query against its definition.
+tests/test_oracle_mutants.py checks that the pins reject copies of
+gj_oracle.c with planted mistakes.
 """
 from __future__ import annotations
 
@@ -65,7 +68,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # GJ_ORACLE_LIB names a separately compiled copy of gj_oracle.c;
+            # tests/test_oracle_mutants.py points it at copies with planted
+            # mistakes to check that the pins reject each one
+            lib = ctypes.CDLL(os.environ.get("GJ_ORACLE_LIB") or build())
             u32p = ctypes.POINTER(ctypes.c_uint32)
             i8p = ctypes.POINTER(ctypes.c_int8)
             i64p = ctypes.POINTER(ctypes.c_int64)
@@ -103,6 +109,8 @@ def _load():
             lib.og_delta.restype = ctypes.c_int
             lib.og_delta.argtypes = [vp, vp, u32p, u32p, i8p, ctypes.c_uint64, ctypes.c_uint32, u32p,
                                      ctypes.c_uint32, u32p, i64p, u64p]
+            lib.og_delta_each.restype = ctypes.c_int
+            lib.og_delta_each.argtypes = lib.og_delta.argtypes + [i64p, u64p]
             _lib = lib
     return _lib
 
@@ -291,6 +299,23 @@ def delta(g_old: Graph, g_new: Graph, dsrc, ddst, dsign, q: Query):
     _check(_load().og_delta(g_old._h, g_new._h, ps, pd, pg, len(s), q.k, pa, na, po, ctypes.byref(c),
                             ctypes.byref(h)))
     return c.value, h.value
+
+
+def delta_each(g_old: Graph, g_new: Graph, dsrc, ddst, dsign, q: Query):
+    """(count, checksum) of each delta query dQ_i, i in atom definition order
+    (Section 3.3.1); their sums are delta()'s result."""
+    s, ps = _u32(dsrc)
+    d, pd = _u32(ddst)
+    g, pg = _i8(dsign)
+    c = ctypes.c_int64(0)
+    h = ctypes.c_uint64(0)
+    pa, na, po = q._args()
+    ec = np.zeros(max(na, 1), np.int64)
+    eh = np.zeros(max(na, 1), np.uint64)
+    _check(_load().og_delta_each(g_old._h, g_new._h, ps, pd, pg, len(s), q.k, pa, na, po, ctypes.byref(c),
+                                 ctypes.byref(h), ec.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 eh.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+    return [(int(ec[i]), int(eh[i])) for i in range(na)]
 
 
 def apply_batch(g: Graph, src, dst, sign):

@@ -740,11 +740,13 @@ og_graph* og_graph_apply(const og_graph* g, const uint32_t* dsrc, const uint32_t
  * attribute order that starts with the attributes of atom i (source, then
  * destination) followed by the remaining attributes in the query's order
  * (or in ascending attribute id when order is NULL), seeded from each
- * signed change; every match counts with its seed's sign.
+ * signed change; every match counts with its seed's sign. each_count and
+ * each_chk (may be NULL) receive the result of each dQ_i, i = 0..natoms-1.
  */
-int og_delta(const og_graph* g_old, const og_graph* g_new, const uint32_t* dsrc, const uint32_t* ddst,
-             const int8_t* dsign, uint64_t nd, uint32_t k, const uint32_t* atoms, uint32_t natoms,
-             const uint32_t* order, int64_t* dcount, uint64_t* dchk) {
+int og_delta_each(const og_graph* g_old, const og_graph* g_new, const uint32_t* dsrc, const uint32_t* ddst,
+                  const int8_t* dsign, uint64_t nd, uint32_t k, const uint32_t* atoms, uint32_t natoms,
+                  const uint32_t* order, int64_t* dcount, uint64_t* dchk, int64_t* each_count,
+                  uint64_t* each_chk) {
     og_query q;
     int rc = make_query(k, atoms, natoms, NULL, 0, NULL, 0, order, &q);
     if (rc) return rc;
@@ -774,10 +776,19 @@ int og_delta(const og_graph* g_old, const og_graph* g_new, const uint32_t* dsrc,
             }
             if (ok) gj_extend(&r, 2);
         }
+        if (each_count) each_count[i] = r.count;
+        if (each_chk) each_chk[i] = r.chk;
         total += r.count;
         tchk += r.chk;
     }
     *dcount = total;
     *dchk = tchk;
     return OG_OK;
+}
+
+/* The sum of the delta queries only (og_delta_each without the parts). */
+int og_delta(const og_graph* g_old, const og_graph* g_new, const uint32_t* dsrc, const uint32_t* ddst,
+             const int8_t* dsign, uint64_t nd, uint32_t k, const uint32_t* atoms, uint32_t natoms,
+             const uint32_t* order, int64_t* dcount, uint64_t* dchk) {
+    return og_delta_each(g_old, g_new, dsrc, ddst, dsign, nd, k, atoms, natoms, order, dcount, dchk, NULL, NULL);
 }

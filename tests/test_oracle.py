@@ -9,6 +9,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import oracle
 from paper_1802_03760_b300.inputs import QUERIES, er_edges
@@ -149,15 +150,17 @@ def test_complete_graph_closed_forms(n):
 
 
 def matrix_counts(A):
-    """Join counts of the shapes as sums of products of adjacency entries."""
-    A2 = A @ A
-    AtA = A.T @ A
-    AAt = A @ A.T
+    """Join counts of the shapes as sums of products of adjacency entries
+    (exact int64 sparse products, so n = 2000 takes milliseconds)."""
+    S = sp.csr_matrix(np.asarray(A, np.int64))
+    A2 = S @ S
+    AtA = S.T @ S
+    AAt = S @ S.T
     return {
-        "triangle": int((A * A2).sum()),                 # sum A12 A23 A13
-        "cyclic-triangle": int(np.trace(A2 @ A)),        # closed directed walks of length 3
-        "diamond": int((A * AtA * AAt).sum()),           # sum_{2,3} A23 (A^T A)_23 (A A^T)_23
-        "4-cycle": int((A2 * AtA).sum()),                # sum_{1,3} (A^2)_13 (A^T A)_13
+        "triangle": int(S.multiply(A2).sum()),                  # sum A12 A23 A13
+        "cyclic-triangle": int((A2 @ S).diagonal().sum()),      # closed directed walks of length 3
+        "diamond": int(S.multiply(AtA).multiply(AAt).sum()),    # sum_{2,3} A23 (A^T A)_23 (A A^T)_23
+        "4-cycle": int(A2.multiply(AtA).sum()),                 # sum_{1,3} (A^2)_13 (A^T A)_13
     }
 
 
@@ -320,6 +323,54 @@ def test_delta_queries_equal_recount(name, seed):
         c1, h1 = g2.count(q)
         assert oracle.delta(g, g2, cs, cd, cg, q) == (c1 - c0, (h1 - h0) & M64)
         g = g2
+
+
+# shapes with two atoms over the same attribute pair: a seed filter atom of
+# dQ_i reads the new version when it comes before atom i, the old after
+RECIPROCAL = {"2-cycle-tail": (3, [(0, 1), (1, 0), (1, 2)]),
+              "reciprocal-triangle": (3, [(0, 1), (1, 2), (1, 0), (2, 0)])}
+
+
+@pytest.mark.parametrize("name", sorted(QUERIES) + sorted(RECIPROCAL))
+@pytest.mark.parametrize("seed", range(4))
+def test_each_delta_query_brute_force(name, seed):
+    """Section 3.3.1, each part on its own: dQ_i joins the new versions of
+    the atoms before i, the signed changes of atom i and the old versions of
+    the atoms after i. Written out over V^k with A_old, A_new and Delta =
+    A_new - A_old (the batch applied update by update, the last update of an
+    edge deciding). The other telescoping order (old before i, new after)
+    has the same sum, so only the parts tell the two apart."""
+    rng = np.random.default_rng(700 + seed)
+    k, atoms = QUERIES[name] if name in QUERIES else RECIPROCAL[name]
+    n = 6 if k <= 4 else 5
+    A_old = rng.random((n, n)) < 0.45
+    np.fill_diagonal(A_old, False)
+    s, d = np.nonzero(A_old)
+    g = oracle.Graph(n, s, d)
+    b = 30
+    bs, bd, bg = rng.integers(0, n, b), rng.integers(0, n, b), rng.choice([-1, 1], b)
+    A_new = A_old.copy()
+    for u, v, sg in zip(bs, bd, bg):
+        if u != v:
+            A_new[u, v] = sg > 0
+    Dl = A_new.astype(np.int64) - A_old.astype(np.int64)
+    (cs, cd, cg), g2 = oracle.apply_batch(g, bs, bd, bg)
+    assert sorted(zip(cs.tolist(), cd.tolist(), cg.tolist())) == \
+        sorted((int(u), int(v), int(Dl[u, v])) for u, v in zip(*np.nonzero(Dl)))
+    X = np.indices((n,) * k).reshape(k, -1)
+    want = []
+    for i in range(len(atoms)):
+        w = np.ones(X.shape[1], np.int64)
+        for t, (sa, da) in enumerate(atoms):
+            M = A_new if t < i else (A_old if t > i else Dl)
+            w *= M[X[sa], X[da]]
+        chk = 0
+        for c in np.nonzero(w)[0]:
+            chk = (chk + int(w[c]) * py_hash(X[:, c])) & M64
+        want.append((int(w.sum()), chk))
+    q = oracle.Query(k, atoms)
+    assert oracle.delta_each(g, g2, cs, cd, cg, q) == want
+    assert oracle.delta(g, g2, cs, cd, cg, q) == (sum(c for c, _ in want), sum(h for _, h in want) & M64)
 
 
 def test_delta_order_does_not_matter():

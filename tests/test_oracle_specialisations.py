@@ -127,6 +127,24 @@ def test_brute_force_tri_and_inequality_queries(seed):
             assert g.count(q, mode=0) == want, (atoms, lt, o)
 
 
+@pytest.mark.parametrize("n", [4, 6, 9])
+def test_inequality_between_unjoined_attributes_closed_form(n):
+    """Two attributes that no atom joins may take the same vertex, so only a
+    strict inequality between them keeps such tuples out. On the complete
+    directed graph K_n, a -> b <- c with a < c has n * C(n-1, 2) matches
+    (b, then two distinct others in ascending order), whichever of a and c
+    is bound first."""
+    g = graph(~np.eye(n, dtype=bool))
+    atoms = [(0, 1), (2, 1)]
+    want = n * math.comb(n - 1, 2)
+    for lt in ([(0, 2)], [(2, 0)]):
+        for o in itertools.permutations(range(3)):
+            q = oracle.Query(3, atoms, o, lt=lt)
+            assert g.count(q, mode=0)[0] == want, (lt, o)
+            if valid_mode1(3, atoms, [], o):
+                assert g.count(q, mode=1)[0] == want, (lt, o)
+
+
 @pytest.mark.parametrize("name", sorted(SPECIALISED))
 @pytest.mark.parametrize("seed", range(3))
 def test_specialised_formulations_equal_their_shape(name, seed):
