@@ -113,9 +113,12 @@ def test_brute_force_random_queries(seed):
     order = [int(x) for x in rng.permutation(k)]
     n = int(rng.integers(3, 7))
     edges = random_edges(rng, n, float(rng.uniform(0.2, 0.8)))
-    want_c, want_h, _ = brute_force(n, edges, k, atoms)
+    want_c, want_h, want_set = brute_force(n, edges, k, atoms)
     g = og(n, edges)
     assert g.count(oracle.Query(k, atoms, order)) == (want_c, want_h)
+    # a listing is in query attribute order whatever the evaluation order
+    got, h = g.list(oracle.Query(k, atoms, order))
+    assert {tuple(int(x) for x in t) for t in got} == want_set and len(got) == want_c and h == want_h
     # the implementation's evaluation (edge seeds, bound atoms only) on every connected order
     for o in itertools.permutations(range(k)):
         if connected_order(atoms, o):

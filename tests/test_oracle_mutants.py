@@ -129,6 +129,30 @@ MUTANTS = {
     "seed-range-off-by-one": (
         "if (r.x[a0] < first_lo || r.x[a0] >= first_hi) continue;", "if (r.x[a0] < first_lo || r.x[a0] > first_hi) continue;",
         "Theorem 2.1: counts add up over disjoint first-attribute ranges"),
+    "listing-in-execution-order": (
+        "r->out[r->written * q->k + a] = r->x[a];", "r->out[r->written * q->k + a] = r->x[r->order[a]];",
+        "Section 2.1: a match is a tuple over the query's attributes"),
+    "reverse-index-not-transposed": (
+        "uint64_t mr = sorted_keys(dst, src, m, keys);", "uint64_t mr = sorted_keys(src, dst, m, keys);",
+        "Section 4.1: the reverse index holds in-neighbours"),
+    "insertions-not-applied": (
+        "if (dsign[i] > 0) { s[m] = dsrc[i]; d[m] = ddst[i]; m++; }", "(void)0;",
+        "Section 3.3.1: R' = R + Delta R"),
+    "unchanged-edges-kept-as-changes": (
+        "if ((u[i].sign > 0) == present) continue;", "(void)present;",
+        "Section 3.3.1: only updates that change the relation are changes"),
+    "factorisation-reaches-seed": (
+        "    while (f > 2) {", "    while (f > 1) {",
+        "Section 5.4: the seed attributes are not factorised"),
+    "factorisation-needs-three": (
+        "return (q->k - f >= 2) ? f : q->k;", "return (q->k - f >= 3) ? f : q->k;",
+        "Section 5.4: two independent trailing attributes factorise"),
+    "tri-order-unchecked": (
+        "if (r.pos[q.tc[t]] < r.pos[q.ta[t]] || r.pos[q.tc[t]] < r.pos[q.tb[t]]) return OG_E_INVALID;", "(void)0;",
+        "Section 5.4: tri binds its third attribute after its first two"),
+    "unused-attribute-accepted": (
+        "if (used != (1u << k) - 1) return OG_E_INVALID;", "(void)used;",
+        "Section 2.1: every attribute appears in some atom"),
 }
 
 

@@ -285,12 +285,39 @@ def test_factorised_work_units(name, seed):
         assert st2.proposals[j] == sum(min(s) for s in sizes)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_factorised_star_work_units(seed):
+    """The star E(a0, a1), E(a0, a2), E(a0, a3) in the order a0..a3: a1 is
+    joined only to the seed attribute a0, a2 and a3 to no later attribute, so
+    exactly a2 and a3 factorise (the seed pair never does). Each seed edge
+    u -> v is then extended once at both factorised levels, with the single
+    set out(u): extended = |E| and proposals = sum over edges of outdeg(u),
+    while the count is the sum over vertices of outdeg^3."""
+    rng = np.random.default_rng(7100 + seed)
+    n = 14
+    A = rng.random((n, n)) < 0.35
+    np.fill_diagonal(A, False)
+    g = graph(A)
+    q = oracle.Query(4, [(0, 1), (0, 2), (0, 3)], [0, 1, 2, 3])
+    out = A.sum(axis=1).astype(np.int64)
+    c2, _, st2 = g.count(q, stats=True, mode=2)
+    assert c2 == int((out ** 3).sum())
+    m = int(A.sum())
+    for j in (2, 3):
+        assert st2.extended[j] == m
+        assert st2.nbind_sum[j] == m
+        assert st2.proposals[j] == int((out * out).sum())
+
+
 def test_rejects_invalid_specialisations():
     g = graph(np.triu(np.ones((5, 5), bool), 1))
     bad = [
         dict(k=3, atoms=[], tri=[(0, 1, 1)], lt=[], order=None),          # repeated attribute
         dict(k=3, atoms=[], tri=[(0, 1, 2)], lt=[(1, 1)], order=None),    # x < x
         dict(k=3, atoms=[], tri=[(0, 1, 2)], lt=[], order=[2, 0, 1]),     # third attribute first
+        # edge seed (0, 2) and attribute 1 bound by E(0, 1), but tri(0, 1, 2)'s
+        # third attribute comes before its second
+        dict(k=3, atoms=[(0, 2), (0, 1)], tri=[(0, 1, 2)], lt=[], order=[0, 2, 1]),
         dict(k=3, atoms=[], tri=[(0, 1, 3)], lt=[], order=None),          # out of range
     ]
     for sp in bad:
