@@ -159,22 +159,33 @@ def lib():
 
 def _ptr(a, elem: int = 4):
     """(pointer, keepalive) for a 1-D numpy array or sequence (converted to
-    uint32, or int8 when elem == 1), a 1-D contiguous torch tensor with
-    elem-byte elements (host or device), or None."""
+    uint32, or int8 when elem == 1; values the target type cannot hold are
+    refused, not wrapped), a 1-D contiguous integer torch tensor with
+    elem-byte elements (host or device, read as is), or None."""
     if a is None:
         return None, None
     if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
         if a.dim() != 1 or not a.is_contiguous() or a.element_size() != elem:
             raise ValueError("tensor arguments must be 1-D, contiguous, with %d-byte elements" % elem)
+        if a.dtype.is_floating_point or a.dtype.is_complex or str(a.dtype) == "torch.bool":
+            raise ValueError("tensor arguments must hold integers, not %s" % a.dtype)
         if a.is_cuda:
             # the library reads device inputs on its own stream: the work that
             # wrote this tensor (on the current stream) must have finished
             import torch
             torch.cuda.current_stream(a.device).synchronize()
         return ctypes.c_void_p(a.data_ptr()), a
-    arr = np.ascontiguousarray(a, dtype=np.uint32 if elem == 4 else np.int8)
-    if arr.ndim != 1:
+    want = np.dtype(np.uint32 if elem == 4 else np.int8)
+    src = np.asarray(a)
+    if src.ndim != 1:
         raise ValueError("array arguments must be 1-D")
+    if src.dtype != want and src.size:
+        if src.dtype.kind not in "iu":
+            raise ValueError("array arguments must hold integers, not %s" % src.dtype)
+        lo, hi = np.iinfo(want).min, np.iinfo(want).max
+        if int(src.min()) < lo or int(src.max()) > hi:
+            raise ValueError("array values must lie in [%d, %d]" % (lo, hi))
+    arr = np.ascontiguousarray(src, dtype=want)
     return ctypes.c_void_p(arr.ctypes.data), arr
 
 

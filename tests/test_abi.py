@@ -79,6 +79,23 @@ def test_marshalling_rejects_arrays_the_library_would_misread():
         gj._ptr8(t)
     p8, keep8 = gj._ptr8([1, -1, 1])
     assert keep8.dtype == np.int8 and keep8.tolist() == [1, -1, 1]
+    # values a narrower type cannot hold are refused, not wrapped
+    for bad in (np.array([2 ** 32 + 5], np.int64), np.array([-1], np.int64), np.array([1.5, 2.0])):
+        with pytest.raises(ValueError):
+            gj._ptr(bad)
+    for bad in (np.array([257, 1], np.int64), np.array([1, -129])):
+        with pytest.raises(ValueError):
+            gj._ptr8(bad)
+    ok = gj._ptr(np.array([0, 2 ** 32 - 1], np.int64))[1]
+    assert ok.dtype == np.uint32 and ok.tolist() == [0, 2 ** 32 - 1]
+    assert gj._ptr(np.zeros(0))[1].dtype == np.uint32  # empty: nothing to range-check
+    # float and bool tensors of the right element size are refused too
+    for bad in (torch.zeros(4, dtype=torch.float32),):
+        with pytest.raises(ValueError):
+            gj._ptr(bad)
+    for bad in (torch.ones(4, dtype=torch.bool),):
+        with pytest.raises(ValueError):
+            gj._ptr8(bad)
 
 
 def test_tensor_on_another_device_is_refused_before_any_call():
