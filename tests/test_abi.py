@@ -122,3 +122,38 @@ def test_load_and_query_extensions_reject_bad_arguments_without_device_work():
     assert L.gj_query_define_ex(None, 3, None, 0, None, 0, None, 0, None, None) == -1
     assert L.gj_graph_build_triangles(None, None) == -1
     assert L.gj_graph_relabel_map(None, None) == -1
+
+
+def test_plain_c_program_compiles_links_and_calls_the_library(tmp_path):
+    """The boundary is a C ABI: a C99 program that includes only include/gj.h
+    compiles with -pedantic -Werror, links against libgj.so and calls the
+    entry points that need no device (error names, build kind, argument
+    checks on null handles)."""
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc is not installed")
+    path = build()
+    libdir = os.path.dirname(path)
+    inc = os.path.dirname(gj.HEADER)
+    src = tmp_path / "consumer.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "gj.h"
+int main(void) {
+    int64_t c = 0;
+    uint64_t h = 0;
+    printf("%s|%d|%d|%d\n", gj_strerror(GJ_E_INVALID), gj_checked_build(),
+           gj_count(NULL, NULL, &c, &h), gj_graph_stats(NULL, NULL, NULL));
+    return 0;
+}
+''')
+    exe = tmp_path / "consumer"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src),
+                           "-L", libdir, "-lgj", "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    name, checked, rc_count, rc_stats = out.stdout.strip().split("|")
+    assert name == gj.lib().gj_strerror(-1).decode()
+    assert (int(checked), int(rc_count), int(rc_stats)) == (0, -1, -1)
