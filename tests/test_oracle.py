@@ -400,6 +400,24 @@ def test_rejects_invalid():
         oracle.Graph(4, np.array([0], np.uint32), np.array([4], np.uint32))
 
 
+def test_edge_seeded_mode_needs_each_attribute_bound_by_earlier_ones():
+    """The path a0 -> a1 -> a2 -> a3 in the order a0, a1, a3, a2: the seed
+    pair (a0, a1) is an atom, but when a3 comes no atom joins it to a bound
+    attribute. The definition (mode 0) extends by the projection and still
+    counts every path; the edge-seeded evaluation (Section 4.1) has no
+    relation to propose a3 from and refuses the order."""
+    rng = np.random.default_rng(11)
+    n = 6
+    edges = random_edges(rng, n, 0.5)
+    k, atoms, order = 4, [(0, 1), (1, 2), (2, 3)], [0, 1, 3, 2]
+    want_c, want_h, _ = brute_force(n, edges, k, atoms)
+    g = og(n, edges)
+    assert g.count(oracle.Query(k, atoms, order), mode=0) == (want_c, want_h)
+    with pytest.raises(oracle.OracleError):
+        g.count(oracle.Query(k, atoms, order), mode=1)
+    assert g.count(oracle.Query(k, atoms, [0, 1, 2, 3]), mode=1) == (want_c, want_h)
+
+
 def test_empty_graph():
     g = oracle.Graph(5, np.array([], np.uint32), np.array([], np.uint32))
     assert g.m == 0

@@ -153,6 +153,32 @@ MUTANTS = {
     "unused-attribute-accepted": (
         "if (used != (1u << k) - 1) return OG_E_INVALID;", "(void)used;",
         "Section 2.1: every attribute appears in some atom"),
+    "unbound-level-accepted": (
+        "                if (r.pos[q.tc[t]] == j) ok = 1;\n            if (!ok) return OG_E_INVALID;",
+        "                if (r.pos[q.tc[t]] == j) ok = 1;\n            (void)ok;",
+        "Section 4.1: every later attribute is bound by an atom over earlier ones"),
+    "sign-unchecked": (
+        "if (sign[i] != 1 && sign[i] != -1) { free(u); return OG_E_INVALID; }", "(void)0;",
+        "Section 3.3.1: an update inserts (+1) or deletes (-1)"),
+    "equal-attribute-atom-accepted": (
+        "if (q->as[t] >= k || q->ad[t] >= k || q->as[t] == q->ad[t]) return OG_E_INVALID;",
+        "if (q->as[t] >= k || q->ad[t] >= k) return OG_E_INVALID;",
+        "Section 2.1: an edge atom joins two distinct attributes"),
+    "tri-seed-one-way": (
+        "if ((q.ta[t] == a0 && q.tb[t] == a1) || (q.ta[t] == a1 && q.tb[t] == a0))",
+        "if (q.ta[t] == a0 && q.tb[t] == a1)",
+        "Section 5.4: a tri atom's key pair seeds in either order"),
+    "degree-is-in-degree": (
+        "key[v] = degree_order ? (((uint64_t)(h->fo[v + 1] - h->fo[v]) << 32) | v) : (uint64_t)v;",
+        "key[v] = degree_order ? (((uint64_t)(h->ro[v + 1] - h->ro[v]) << 32) | v) : (uint64_t)v;",
+        "Section 5.4: renaming by (out-)degree"),
+    "edge-seed-one-way": (
+        "if ((q.as[t] == a0 && q.ad[t] == a1) || (q.as[t] == a1 && q.ad[t] == a0))",
+        "if (q.as[t] == a0 && q.ad[t] == a1)",
+        "Section 4.2: an edge atom over the first two attributes seeds in either direction"),
+    "delta-seed-ignores-sign": (
+        "            r.sign = dsign[c];", "            r.sign = 1;",
+        "Section 3.3.1: each match counts with its seed's sign"),
 }
 
 

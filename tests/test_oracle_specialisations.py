@@ -237,6 +237,15 @@ def test_degree_renaming(seed):
         (int(want_map[u]), int(want_map[v])) for u, v in zip(us, vs) if want_map[u] < want_map[v]}
     gi, mi = g0.transform()
     assert np.array_equal(mi, np.arange(n)) and gi.m == g0.m
+    # without symmetrisation the renaming ascends with the out-degree of the directed graph
+    dout = A.sum(1)
+    rank_d = sorted(range(n), key=lambda v: (dout[v], v))
+    want_d = np.empty(n, np.int64)
+    want_d[rank_d] = np.arange(n)
+    gd, md = g0.transform(degree_order=True)
+    assert np.array_equal(md, want_d)
+    s0, d0 = np.nonzero(A)
+    assert set(zip(*[x.tolist() for x in gd.edges()])) == {(int(want_d[u]), int(want_d[v])) for u, v in zip(s0, d0)}
 
 
 @pytest.mark.parametrize("name", ["diamond-f", "house-f", "house-tr"])
