@@ -31,6 +31,7 @@ LOAD_ORIENT = 4
 ERRORS = {
     -1: "GJ_E_INVALID", -2: "GJ_E_RANGE", -3: "GJ_E_NOMEM", -4: "GJ_E_ADMIT", -5: "GJ_E_TRUNCATED",
     -6: "GJ_E_TIMEOUT", -7: "GJ_E_OVERFLOW", -8: "GJ_E_CUDA", -9: "GJ_E_PENDING", -10: "GJ_E_NOTFOUND",
+    -11: "GJ_E_CHECK", -12: "GJ_E_CANCELLED",
 }
 
 

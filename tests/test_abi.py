@@ -157,3 +157,23 @@ int main(void) {
     name, checked, rc_count, rc_stats = out.stdout.strip().split("|")
     assert name == gj.lib().gj_strerror(-1).decode()
     assert (int(checked), int(rc_count), int(rc_stats)) == (0, -1, -1)
+
+
+def test_error_names_match_the_header():
+    """The binding names every GJ_E_* code of include/gj.h with the header's value."""
+    import re
+    text = open(gj.HEADER).read()
+    codes = {int(v): n for n, v in re.findall(r"\b(GJ_E_[A-Z]+)\s*=\s*(-\d+)", text)}
+    assert codes and gj.ERRORS == codes
+
+
+def test_missing_library_raises_instead_of_falling_back(tmp_path, monkeypatch):
+    """Without the built library the binding refuses to run: there is no
+    other implementation to fall back to."""
+    import pytest
+    monkeypatch.setattr(gj, "LIB_PATH", str(tmp_path / "libgj.so"))
+    monkeypatch.setattr(gj, "_lib", None)
+    with pytest.raises(ImportError, match="not built"):
+        gj.lib()
+    with pytest.raises(ImportError):
+        gj.Context(0)
