@@ -105,3 +105,18 @@ def test_traffic_only_from_a_capture_of_the_current_kernel(tmp_path, monkeypatch
     assert bench.profiled_traffic()[0] == 1234
     f.write_text("kernel_sources_sha256: %s\ntraffic_bytes_per_launch: 1234\n" % ("0" * 64))
     assert bench.profiled_traffic() == (None, "kernel changed since the ncu capture")
+
+
+def test_a_failing_sub_record_keeps_the_headline(capsys):
+    """bench.sub_record returns the record, or on failure an error entry
+    (and a stderr line) instead of raising, so the headline line is printed."""
+    import bench
+
+    assert bench.sub_record("delta", lambda x, y=1: {"v": x + y}, 2, y=3) == {"v": 5}
+
+    def boom():
+        raise RuntimeError("no box")
+
+    r = bench.sub_record("serve", boom)
+    assert r == {"error": "RuntimeError: no box"}
+    assert "the serve record failed" in capsys.readouterr().err
