@@ -177,7 +177,7 @@ int gj_create(int cuda_device, const gj_options* opt, gj_ctx** out) {
     *out = nullptr;
     if (cuda_device < 0) return GJ_E_INVALID;
     int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {  // no usable driver or device
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {  // no usable CUDA driver or device
         cudaGetLastError();
         return GJ_E_CUDA;
     }

@@ -106,7 +106,7 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // of each aggregated group [FC]. A warp finishes a last-level batch before
 // it activates another one, so one block serves every query. Offsets are
 // closed forms so that no per-level table sits in local memory. The
-// footprint is kept small on purpose: the driver gives an SM's unified L1 /
+// footprint is kept small on purpose: the CUDA driver gives an SM's L1 /
 // shared memory the smallest shared-memory size that holds the resident
 // blocks, and the rest is L1 for the probed lists and hash sets (four
 // extended k = 4 blocks fit 196 KB, leaving about 60 KB of L1).

@@ -120,3 +120,13 @@ def test_a_failing_sub_record_keeps_the_headline(capsys):
     r = bench.sub_record("serve", boom)
     assert r == {"error": "RuntimeError: no box"}
     assert "the serve record failed" in capsys.readouterr().err
+
+
+def test_kernel_sha_ignores_comments_but_not_code():
+    """The ncu capture stays valid across comment edits and not across code edits."""
+    import bench
+
+    src = "// layout\nint f(int x) { /* twice */ return 2 * x; }  // end\n\n"
+    assert bench.code_only(src) == "int f(int x) {  return 2 * x; }"
+    assert bench.code_only(src.replace("twice", "double").replace("layout", "the layout")) == bench.code_only(src)
+    assert bench.code_only(src.replace("2 * x", "3 * x")) != bench.code_only(src)
