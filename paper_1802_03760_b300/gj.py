@@ -213,6 +213,7 @@ class Context:
     def __init__(self, device: int = 0, prefix_buffer_bytes: int = 0, window: int = 0, engine: int = ENGINE_FUSED,
                  stream=None, flags: int = 0):
         self._h = None
+        self._server = None  # weakref to the context's running Server, if any
         o = Options(prefix_buffer_bytes, window, engine, flags, ctypes.c_void_p(stream) if stream else None)
         h = _VP()
         _check(lib().gj_create(device, ctypes.byref(o), ctypes.byref(h)))
@@ -220,8 +221,18 @@ class Context:
         self.device = device
         self._children = weakref.WeakSet()  # graphs and queries, freed before the context
 
+    def _stop_server(self):
+        """Stops the context's request loop (which may still read its graph
+        and the queries of pending requests) before any of them is freed."""
+        ref = getattr(self, "_server", None)
+        s = ref() if ref is not None else None
+        if s is not None:
+            s.stop()
+        self._server = None
+
     def close(self):
         if self._h:
+            self._stop_server()
             for c in list(self._children):
                 c.free()
             lib().gj_destroy(self._h)
@@ -293,6 +304,7 @@ class Graph:
 
     def free(self):
         if self._h:
+            self.ctx._stop_server()  # gj_graph_free would stop it too, unseen by the Server object
             lib().gj_graph_free(self._h)
             self._h = None
 
@@ -341,6 +353,10 @@ class Query:
 
     def free(self):
         if self._h:
+            ref = getattr(self.ctx, "_server", None)
+            s = ref() if ref is not None else None
+            if s is not None and any(q is self for qs in s._keep.values() for q in qs):
+                s.stop()  # a pending request still reads this query: finish the requests first
             lib().gj_query_free(self._h)
             self._h = None
 
@@ -446,8 +462,10 @@ class Server:
         self.g = g
         self.ctx = g.ctx
         self._keep = {}
+        self.running = False
         _check(lib().gj_serve_start(self.ctx._h, g._h, memory_budget_bytes), self.ctx)
         self.running = True
+        self.ctx._server = weakref.ref(self)
 
     def submit_count(self, qs) -> int:
         arr = (_VP * len(qs))(*[q._h for q in qs])
@@ -489,9 +507,22 @@ class Server:
         return r.as_dict()
 
     def stop(self):
+        """gj_serve_stop: finishes every submitted request, then ends the loop."""
         if self.running:
-            _check(lib().gj_serve_stop(self.ctx._h), self.ctx)
             self.running = False
+            _check(lib().gj_serve_stop(self.ctx._h), self.ctx)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
 
 
 def list_matches(g: Graph, q: Query, cap: int):
