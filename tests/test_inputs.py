@@ -130,3 +130,79 @@ def test_mixed_queries():
         assert I.connected_order(atoms, order)
     assert mq == I.mixed_queries(64, seed=3)
     assert mq[5:] != I.mixed_queries(64, seed=4)[5:]
+
+
+# The recipe restated in plain Python, draw by draw: SplitMix64 output of
+# state seed + (ctr + 1) * 0x9e3779b97f4a7c15; stream seeds subseed(seed, tag)
+# = draw tag of stream seed; uniform integers below a bound by multiply-high.
+M64 = (1 << 64) - 1
+GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+
+
+def py_mix64(z):
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def py_rand(seed, ctr):
+    return py_mix64((seed + (ctr + 1) * GOLDEN_GAMMA) & M64)
+
+
+def py_below(r, bound):
+    return (r * bound) >> 64
+
+
+def test_rmat_samples_follow_the_recipe_exactly():
+    """Sample e, level l: a 53-bit uniform from draw e * 64 + l of stream
+    subseed(seed, 2) picks the quadrant (a, b, c, d); the first level sets
+    the most significant bit; ids then pass through the permutation of
+    stream subseed(seed, 7)."""
+    scale, seed, count = 12, 1, 96
+    a, b, c = I.RMAT_ABC
+    st = py_rand(seed, 2)
+    s, d = I.rmat_edges(scale, seed=seed, permute=False, count=count)
+    for e in range(count):
+        u = v = 0
+        for lvl in range(scale):
+            x = (py_rand(st, e * 64 + lvl) >> 11) * (1.0 / 9007199254740992.0)
+            q = 0 if x < a else 1 if x < a + b else 2 if x < a + b + c else 3
+            u, v = (u << 1) | (q >> 1), (v << 1) | (q & 1)
+        assert (int(s[e]), int(d[e])) == (u, v), e
+    ps, pd = I.rmat_edges(scale, seed=seed, count=count)
+    perm = I.permutation(1 << scale, py_rand(seed, 7))
+    assert np.array_equal(ps, perm[s]) and np.array_equal(pd, perm[d])
+
+
+def test_permutation_is_fisher_yates_on_the_stream():
+    n, seed = 1000, 12345
+    want = list(range(n))
+    for i in range(n, 1, -1):
+        j = py_below(py_rand(seed, i), i)
+        want[i - 1], want[j] = want[j], want[i - 1]
+    assert I.permutation(n, seed).tolist() == want
+
+
+def test_er_draws_follow_the_recipe_exactly():
+    """Draw ctr of stream subseed(seed, 1) gives u from its low and v from its
+    high 32 bits, each scaled to [0, n) by multiply-high; pairs with u == v
+    and repeats are skipped."""
+    n, m, seed = 37, 300, 9
+    st = py_rand(seed, 1)
+    want, seen, ctr = [], set(), 0
+    while len(want) < m:
+        r = py_rand(st, ctr)
+        ctr += 1
+        u, v = ((r & 0xFFFFFFFF) * n) >> 32, ((r >> 32) * n) >> 32
+        if u != v and (u, v) not in seen:
+            seen.add((u, v))
+            want.append((u, v))
+    s, d = I.er_edges(n, m, seed=seed)
+    assert list(zip(s.tolist(), d.tolist())) == want
+
+
+def test_uniform_draws_follow_the_recipe_exactly():
+    bound, seed, first = 1_000_003, 77, 5
+    got = I.uniform(bound, 40, seed, first=first)
+    assert got.tolist() == [py_below(py_rand(seed, first + i), bound) for i in range(40)]
+    assert I.subseed(seed, 3) == py_rand(seed, 3)
