@@ -206,3 +206,37 @@ def test_uniform_draws_follow_the_recipe_exactly():
     got = I.uniform(bound, 40, seed, first=first)
     assert got.tolist() == [py_below(py_rand(seed, first + i), bound) for i in range(40)]
     assert I.subseed(seed, 3) == py_rand(seed, 3)
+
+
+def test_hubs_follow_the_recipe_exactly():
+    """Hub ids: distinct draws below n from stream subseed(seed, 11). Hub h's
+    out- (t = 2h) and in-neighbours (t = 2h + 1): distinct draws below n,
+    skipping the hub, from the stream seeded subseed(seed, 12) xor
+    0x5bd1e995 * (t + 1)."""
+    n, nh, deg, seed = 500, 3, 40, 8
+    ids, ctr = [], 0
+    while len(ids) < nh:
+        x = py_below(py_rand(py_rand(seed, 11), ctr), n)
+        ctr += 1
+        if x not in ids:
+            ids.append(x)
+    base = py_rand(seed, 12)
+    want_s, want_d = [], []
+    for t in range(2 * nh):
+        hub = ids[t // 2]
+        st = base ^ ((0x5BD1E995 * (t + 1)) & M64)
+        seen, got, ctr = {hub}, [], 0
+        while len(got) < deg:
+            x = py_below(py_rand(st, ctr), n)
+            ctr += 1
+            if x not in seen:
+                seen.add(x)
+                got.append(x)
+        if t % 2:
+            want_s += got
+            want_d += [hub] * deg
+        else:
+            want_s += [hub] * deg
+            want_d += got
+    gi, gs, gd = I.hub_edges(n, nh, deg, seed=seed)
+    assert gi.tolist() == ids and gs.tolist() == want_s and gd.tolist() == want_d
