@@ -123,3 +123,22 @@ def test_libraries_export_disjoint_symbols():
     assert not any(s.startswith("og_") for s in lib)
     assert not any(s.startswith("gj_") for s in ora)
     assert {"og_count_ex", "og_delta_each"} <= ora and {"gj_count_many", "gj_apply_batch"} <= lib
+
+
+def test_golden_writers_call_only_the_oracle():
+    """Every stored expected value is written by a script that uses the
+    oracle and the input generators only: no CUDA binding, no torch."""
+    gdir = os.path.join(ROOT, "tests", "golden")
+    scripts = sorted(f for f in os.listdir(gdir) if f.endswith(".py"))
+    assert scripts
+    for f in scripts:
+        tree = ast.parse(open(os.path.join(gdir, f)).read())
+        mods = set()
+        for node in ast.walk(tree):
+            if isinstance(node, ast.Import):
+                mods |= {a.name for a in node.names}
+            elif isinstance(node, ast.ImportFrom):
+                mods.add(node.module or "")
+        pkg = {m for m in mods if m.startswith("paper_1802_03760_b300")}
+        assert pkg <= {"paper_1802_03760_b300.inputs"}, (f, pkg)
+        assert "oracle" in mods and not any(m.split(".")[0] == "torch" for m in mods), (f, mods)
