@@ -5,7 +5,8 @@ its Python wrapper imports nothing from the package; the two shared
 libraries export disjoint symbol sets; and in bench.py and
 __graft_entry__.py the oracle is imported only inside the CPU-baseline
 sampler, build() and smoke(). The seeded input generators are the one module
-both sides use, and it imports neither of them. CPU only."""
+both sides use, and it imports neither of them; the scripts that write the
+stored goldens use only the oracle and those generators. CPU only."""
 import ast
 import os
 import re
